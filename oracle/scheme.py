@@ -1,0 +1,125 @@
+"""Oracle residual L(W) (Eq. 4), SSP-RK3 (Section 4) and the CFL time step.
+
+Test infrastructure only (see oracle/__init__.py).
+
+L(W)_i = -(1/|Omega_i|) sum_p |l_p| sum_k omega_k F(x_pk) . n_p with
+omega_1 = omega_2 = 1/2 (Eq. 5).  Each face flux uses the Gauss-point values
+of the two cells on its sides; at an outflow boundary face both states are
+the inner cell's value (reading: ghost = copy of the cell, so HLLC returns the
+physical flux of the inner state).
+
+Non-physical states (rho <= 0, p <= 0 or not finite at a Gauss point) raise
+NonPhysicalState; the paper has no positivity limiter.
+
+Time step (reading, the paper only states dt = 0.3 h for its accuracy runs):
+dt = CFL * min_i 2|Omega_i| / sum_p (|v_i . n_p| + c_i) |l_p| with c = 0 for
+scalar advection.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .flux import hllc_flux, upwind_flux, pressure
+from .mesh import OracleMesh
+from .reconstruction import Params, precompute
+from .weno import gauss_values_group
+
+__all__ = ["OracleSolver", "NonPhysicalState"]
+
+
+class NonPhysicalState(ArithmeticError):
+    pass
+
+
+class OracleSolver:
+    def __init__(self, mesh: OracleMesh, params: Params | None = None):
+        self.mesh = mesh
+        self.params = params or Params()
+        self.groups = precompute(mesh, self.params)
+        self.nv = 4 if self.params.eqn == "euler" else 1
+        m = mesh
+        # Gauss points of the two sides: L uses 2kL, 2kL+1; R meets them at 2kR+1, 2kR
+        self.fL = m.face_L
+        self.fR = m.face_R
+        self.gL = np.stack([2 * m.face_kL, 2 * m.face_kL + 1], axis=1)
+        self.gR = np.stack([2 * m.face_kR + 1, 2 * m.face_kR], axis=1)
+        self.boundary = m.face_R < 0
+
+    def gauss_values(self, W: np.ndarray) -> np.ndarray:
+        Wg = np.full((self.nv, self.mesh.n_cells, 8), np.nan)
+        for t in self.groups:
+            Wg[:, t.cells, :t.G] = gauss_values_group(t, W, self.params)
+        return Wg
+
+    def face_fluxes(self, W: np.ndarray) -> np.ndarray:
+        """F_f = |l_f|/2 (F(x_f1) + F(x_f2)), normal pointing from L to R: (nv, n_faces)."""
+        m = self.mesh
+        Wg = self.gauss_values(W)
+        R = np.where(self.boundary, self.fL, self.fR)
+        gR = np.where(self.boundary[:, None], self.gL, self.gR)
+        WL = Wg[:, self.fL[:, None], self.gL]               # (nv, Nf, 2)
+        WR = Wg[:, R[:, None], gR]
+        self._check(WL)
+        self._check(WR)
+        nx = m.face_normal[:, 0][:, None]
+        ny = m.face_normal[:, 1][:, None]
+        if self.params.eqn == "euler":
+            F = hllc_flux(WL, WR, nx, ny, self.params.gas_gamma)
+        else:
+            F = upwind_flux(WL, WR, nx, ny, self.params.adv)
+        return 0.5 * m.face_len[None, :] * (F[..., 0] + F[..., 1])
+
+    def _check(self, Wq):
+        if not np.all(np.isfinite(Wq)):
+            raise NonPhysicalState("non-finite value at a Gauss point")
+        if self.params.eqn == "euler":
+            if np.any(Wq[0] <= 0.0) or np.any(pressure(Wq, self.params.gas_gamma) <= 0.0):
+                raise NonPhysicalState("rho <= 0 or p <= 0 at a Gauss point")
+
+    def residual(self, W: np.ndarray) -> np.ndarray:
+        """L(W) of Eq. (4): (nv, n_cells)."""
+        F = self.face_fluxes(W)
+        acc = np.zeros_like(W)
+        np.add.at(acc, (slice(None), self.fL), -F)
+        inner = ~self.boundary
+        np.add.at(acc, (slice(None), self.fR[inner]), F[:, inner])
+        return acc / self.mesh.area[None, :]
+
+    def rk3_step(self, W: np.ndarray, dt: float, L=None) -> np.ndarray:
+        """Third-order TVD Runge-Kutta step of Section 4."""
+        L = L or self.residual
+        W1 = W + dt * L(W)
+        W2 = 0.75 * W + 0.25 * W1 + 0.25 * dt * L(W1)
+        return W / 3.0 + 2.0 / 3.0 * W2 + 2.0 / 3.0 * dt * L(W2)
+
+    def max_dt(self, W: np.ndarray, cfl: float) -> float:
+        m = self.mesh
+        if self.params.eqn == "euler":
+            rho = W[0]
+            u = W[1] / rho
+            v = W[2] / rho
+            c = np.sqrt(self.params.gas_gamma * pressure(W, self.params.gas_gamma) / rho)
+        else:
+            u = np.full(m.n_cells, self.params.adv[0])
+            v = np.full(m.n_cells, self.params.adv[1])
+            c = np.zeros(m.n_cells)
+        nx, ny = m.face_normal[:, 0], m.face_normal[:, 1]
+        s = np.zeros(m.n_cells)
+        L = self.fL
+        np.add.at(s, L, (np.abs(u[L] * nx + v[L] * ny) + c[L]) * m.face_len)
+        inner = ~self.boundary
+        R = self.fR[inner]
+        np.add.at(s, R, (np.abs(u[R] * nx[inner] + v[R] * ny[inner]) + c[R]) * m.face_len[inner])
+        return float(cfl * np.min(2.0 * m.area / s))
+
+    def conservation(self, W: np.ndarray) -> np.ndarray:
+        return (W * self.mesh.area[None, :]).sum(axis=1)
+
+    def run(self, W: np.ndarray, t_end: float, cfl: float):
+        """Step to t_end with N = ceil(t_end / dt_cfl) equal steps (dt from the initial state)."""
+        dt0 = self.max_dt(W, cfl)
+        n = int(np.ceil(t_end / dt0 - 1e-12))
+        dt = t_end / n
+        for _ in range(n):
+            W = self.rk3_step(W, dt)
+        return W, n, dt

@@ -1,0 +1,130 @@
+"""Oracle precompute (Sections 3.1-3.3) pinned by exact reproduction and the paper's identities."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import synthetic as S
+from oracle import OracleMesh, Params, precompute
+from oracle.mesh import SLOT_GHOST
+from oracle.reconstruction import _d_weights
+from oracle.weno import gauss_values_group
+
+
+def _quadratic(x, y):
+    return (1.0 + 2.0 * x - 3.0 * y + 4.0 * x * x - 5.0 * x * y + 6.0 * y * y)[None]
+
+
+def _linear(x, y):
+    return (0.7 - 1.3 * x + 2.1 * y)[None]
+
+
+def _no_ghost_rows(mesh, t):
+    return np.array([all(s[0] != SLOT_GHOST for s in mesh.slots[c]) for c in t.cells])
+
+
+@pytest.fixture(scope="module", params=["quad", "tri", "mixed"])
+def outflow_case(request):
+    mi = S.mesh_for_config(3, n=9, seed=5, kind=request.param)
+    mesh = OracleMesh.from_input(mi)
+    return mi, mesh, precompute(mesh, Params())
+
+
+def test_p2_reproduces_a_global_quadratic(outflow_case):
+    """P^2(x_G) = sum_j eta_j W_ij is exact for quadratics (Eq. 13), with and without d_j."""
+    mi, mesh, groups = outflow_case
+    W = S.cell_average(mi, _quadratic, order=4)[0]   # independent Duffy quadrature
+    checked = 0
+    for t in groups:
+        ok = _no_ghost_rows(mesh, t)
+        xG = mesh.cell_gauss[t.cells, :t.G]
+        exact = _quadratic(xG[..., 0], xG[..., 1])[0]
+        Ws = W[t.slot_cells]                              # (N, M+1)
+        for eta in (t.eta_raw, t.eta):
+            approx = np.einsum("ngj,nj->ng", eta, Ws)
+            # full-rank least-squares fits reproduce quadratics exactly
+            rank_ok = np.linalg.matrix_rank(t.A) == 5
+            sel = ok & rank_ok
+            assert np.abs(approx[sel] - exact[sel]).max() < 1e-11
+            checked += sel.sum()
+    assert checked > 50
+
+
+def test_candidates_reproduce_linear_functions(outflow_case):
+    mi, mesh, groups = outflow_case
+    W = S.cell_average(mi, _linear, order=3)
+    for t in groups:
+        ok = _no_ghost_rows(mesh, t)
+        W0 = W[0, t.cells]
+        dW = np.stack([W[0, t.members[..., 0]] - W0[:, None], W[0, t.members[..., 1]] - W0[:, None]], -1)
+        g = np.einsum("nmab,nmb->nma", t.grad_op, dW)
+        xG = mesh.cell_gauss[t.cells, :t.G]
+        P = W0[:, None, None] + np.einsum("nma,nga->ngm", g, t.dG)
+        exact = _linear(xG[..., 0], xG[..., 1])[0]
+        err = np.abs(P - exact[..., None])
+        # a candidate whose third cell was replaced by i0 has only one constraint on g_j
+        full = (t.members[..., 1] != t.cells[:, None])[:, None, :]
+        assert np.where(full, err, 0.0)[ok].max() < 1e-12
+        assert full.mean() > 0.5
+
+
+def test_linear_weights_sum_to_one_and_solve_the_system(outflow_case):
+    _, _, groups = outflow_case
+    for t in groups:
+        for gam, eta in ((t.gamma_raw, t.eta_raw), (t.gamma, t.eta)):
+            assert np.abs(gam.sum(-1) - 1.0).max() < 1e-10          # Section 3.1: sum gamma_j = 1
+            res = np.einsum("ngrm,ngm->ngr", t.B, gam) - eta
+            scale = 1.0 + np.abs(gam).max(-1, keepdims=True)
+            assert np.abs(res / scale).max() < 1e-11                 # B gamma = eta (Eq. 15)
+
+
+def test_gamma_is_the_minimum_norm_solution(outflow_case):
+    """gamma lies in the row space of B: orthogonal to null(B) (scipy's own SVD routine)."""
+    _, _, groups = outflow_case
+    for t in groups:
+        for n in range(0, len(t.cells), 7):
+            for g in range(t.G):
+                Z = scipy.linalg.null_space(t.B[n, g], rcond=1e-12)
+                gam = t.gamma[n, g]
+                assert np.abs(Z.T @ gam).max() < 1e-9 * max(1.0, np.abs(gam).max())
+                # same solution from the QR-based minimum-norm driver
+                x = scipy.linalg.lstsq(t.B[n, g], t.eta[n, g], cond=1e-12, lapack_driver="gelsy")[0]
+                assert np.allclose(x, gam, atol=1e-9 * max(1.0, np.abs(gam).max()))
+
+
+def test_linear_scheme_equals_p2_for_any_data(outflow_case):
+    """R(x_G) = sum gamma_j P^1_j(x_G) = P^2(x_G) for arbitrary data (Eq. 14), via the run-time path."""
+    mi, mesh, groups = outflow_case
+    rng = np.random.default_rng(0)
+    W = rng.normal(size=(1, mesh.n_cells))
+    for t in groups:
+        R = gauss_values_group(t, W, Params(linear=True))[0]
+        P2 = np.einsum("ngj,nj->ng", t.eta, W[0][t.slot_cells])
+        assert np.abs(R - P2).max() < 1e-10
+
+
+def test_weighting_parameters_of_section_3_3():
+    g = np.zeros(12)
+    g[4] = 5.0     # gamma_5
+    g[8] = -0.5    # gamma_9
+    g[11] = -4.0   # gamma_12
+    g[0] = 100.0   # gamma_1: first tier keeps d = 1
+    d = _d_weights(g, quad=True)
+    assert d[0] == 1.0 and d[4] == pytest.approx(0.2) and d[8] == 1.0 and d[11] == pytest.approx(0.25)
+    t = np.zeros(9)
+    t[3] = 2.0     # gamma_4 pairs with gamma_8
+    t[7] = -8.0
+    t[5] = 0.5     # gamma_6 pairs with gamma_7
+    d = _d_weights(t, quad=False)
+    assert d[3] == pytest.approx(1 / 8) and d[7] == pytest.approx(1 / 8) and d[5] == 1.0 and d[6] == 1.0
+
+
+def test_optimisation_brings_large_weights_to_order_one():
+    """Tables 1-2: raw max|gamma| grows on poor meshes, the optimised maximum is O(1)."""
+    golden = np.loadtxt(__file__.replace("test_oracle_reconstruction.py", "golden/table2_max_gamma_opt.txt"))
+    mi = S.stretched_vortex_mesh(24, frac=0.5, delta=0.4, seed=2)
+    groups = precompute(OracleMesh.from_input(mi), Params())
+    raw = max(np.abs(t.gamma_raw).max() for t in groups)
+    opt = max(np.abs(t.gamma).max() for t in groups)
+    assert raw > 10.0
+    assert opt <= golden.max() * 1.5
+    assert opt < raw / 5
