@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""WENO3 residual + SSP-RK3 benchmark on one GB300 (cell-updates/s, each RK stage counted).
+
+Workload: 2D Euler isentropic vortex (strength 5, periodic [0,10]^2) on the
+~4.0M-cell low-quality mixed mesh (stretched grid with local spacing ratio
+10, interior nodes displaced by up to 0.4 of the local spacing, 30% of the
+quads split into triangles), FP32 reconstruction / weights / flux with a
+compensated (hi + lo) state.  The FP64 path runs the same mesh for the ratio.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "WENO3 cell-updates/s (×RK stages) on 1 GB300, FP32+batched vs FP64 at stated L1 error"
+UNIT = "cell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD_N = 1754
+
+
+def workload_name(n):
+    return (f"isentropic vortex (strength 5, periodic [0,10]^2) on the low-quality mixed mesh n={n} "
+            f"(stretch ratio 10, displacement 0.4h, 30% split)")
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    v = d[k]
+                    return float(v["value"] if isinstance(v, dict) else v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples of one GPU while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = os.path.join("/tmp", f"weno_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.bus_id}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(seconds=10.0, n=60, steps=None):
+    """Time the FP64 CPU oracle on a bounded sample of the workload (same mesh family at size n)."""
+    import synthetic as S
+    from oracle import OracleMesh, OracleSolver, Params
+    mi = S.stretched_vortex_mesh(n, seed=0)
+    sol = OracleSolver(OracleMesh.from_input(mi), Params())
+    W = S.cell_average(mi, S.isentropic_vortex)
+    dt = sol.max_dt(W, 0.5)
+    done = 0
+    t0 = time.perf_counter()
+    while (steps is None and time.perf_counter() - t0 < seconds) or (steps is not None and done < steps):
+        W = sol.rk3_step(W, dt)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": mi.n_cells * 3 * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} RK3 steps of the numpy FP64 oracle on the same mesh family at n={n} "
+                      f"({mi.n_cells} cells), {el:.1f} s, single-threaded elementwise numpy"}, mi.n_cells, el, done
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist, rank, ws
+    return None, 0, 1
+
+
+def run_reference(args):
+    dist, rank, ws = None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import synthetic as S
+    from oracle import OracleMesh, OracleSolver, Params
+    n = 60
+    mi = S.stretched_vortex_mesh(n, seed=0)
+    sol = OracleSolver(OracleMesh.from_input(mi), Params())
+    W = S.cell_average(mi, S.isentropic_vortex)
+    dt = sol.max_dt(W, 0.5)
+    for _ in range(args.warmup):
+        W = sol.rk3_step(W, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W = sol.rk3_step(W, dt)
+    el = time.perf_counter() - t0
+    v = mi.n_cells * 3 * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(WORKLOAD_N), "sample_n": n, "sample_cells": mi.n_cells,
+                       "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step = one RK3 step of the numpy FP64 oracle on the same mesh family "
+                                       f"at n={n} ({mi.n_cells} cells)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def k1_bytes(nQ, nT, nv, esz, comp):
+    """Algorithmic bytes of one reconstruction pass (tables + one state read + Gauss-value writes)."""
+    def per(M, G):
+        state = nv * esz * (2 if comp else 1)
+        return state + 4 * M + 4 * M * esz + 2 * G * esz + G * M * esz + esz + G * nv * esz
+    return nQ * per(12, 8) + nT * per(9, 6)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=WORKLOAD_N, help="mesh size parameter (default: the 4.0M-cell mesh)")
+    ap.add_argument("--fp64-steps", type=int, default=None, help="FP64 steps (default: min(steps, 20))")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    import torch
+    dist, rank, ws = dist_setup()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()[0]
+
+    import synthetic as S
+    from paper_1712_08317_gb300.api import Mesh, Solver
+    t_setup = time.perf_counter()
+    mi = S.stretched_vortex_mesh(args.n, seed=rank)
+    mesh = Mesh.from_input(mi)
+    W0 = S.cell_average(mi, S.isentropic_vortex, order=4)
+    sol = Solver(mesh, eqn="euler", precision="fp32c")
+    t_setup = time.perf_counter() - t_setup
+    N = mesh.n_cells
+    nQ, nT = int(mesh.info.n_quads), int(mesh.info.n_tris)
+    U, Ul = sol.to_device(W0)
+    dt = float(sol.max_dt(U, Ul, 0.5)[0])
+    if not args.no_autotune:
+        sol.autotune(U, Ul)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sol.step(U, Ul, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    c_start = sol.conservation(U, Ul)[0]
+
+    props = torch.cuda.get_device_properties(dev)
+    bus = f"{getattr(props, 'pci_domain_id', 0):08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    clocks = ClockSampler(bus)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sol.step(U, Ul, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sol.check()
+    c_end = sol.conservation(U, Ul)[0]
+    steps_done = args.warmup + args.steps
+    value = ws * N * 3 * args.steps / (ms / 1e3)
+
+    # dominant kernel alone: the reconstruction pass, timed with events on its stream
+    reps = 20
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    sol.run_pass(1, U, Ul)
+    k0.record(stream)
+    for _ in range(reps):
+        sol.run_pass(1, U, Ul)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    k_ms = k0.elapsed_time(k1) / reps
+    face0 = torch.cuda.Event(enable_timing=True)
+    face1 = torch.cuda.Event(enable_timing=True)
+    face0.record(stream)
+    for _ in range(reps):
+        sol.run_pass(2)
+    face1.record(stream)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(reps):
+        sol.run_pass(3)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    face_ms = face0.elapsed_time(face1) / reps
+    gather_ms = g0.elapsed_time(g1) / reps
+    peak, peak_kind = hbm_peak()
+    kbytes = k1_bytes(nQ, nT, 4, 4, True)
+    achieved = kbytes / (k_ms / 1e3) / 1e9
+
+    # end to end through the public API with host state: H2D copy, step, D2H copy every step
+    hostU = torch.empty(U.shape, dtype=U.dtype, pin_memory=True)
+    hostUl = torch.empty(Ul.shape, dtype=Ul.dtype, pin_memory=True)
+    hostU.copy_(U)
+    hostUl.copy_(Ul)
+    e2e_steps = min(args.steps, 20)
+    torch.cuda.synchronize()
+    x0 = torch.cuda.Event(enable_timing=True)
+    x1 = torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(e2e_steps):
+        U.copy_(hostU, non_blocking=True)
+        Ul.copy_(hostUl, non_blocking=True)
+        sol.step(U, Ul, dt)
+        hostU.copy_(U, non_blocking=True)
+        hostUl.copy_(Ul, non_blocking=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = x0.elapsed_time(x1)
+    steps_done += e2e_steps
+    e2e_value = ws * N * 3 * e2e_steps / (e2e_ms / 1e3)
+    nbytes = U.numel() * 4 * 2
+
+    # FP64 path on the same mesh (tables reused from the mesh's FP64 precompute)
+    fp64_steps = args.fp64_steps if args.fp64_steps is not None else min(args.steps, 20)
+    sol64 = Solver(mesh, eqn="euler", precision="fp64")
+    V, _ = sol64.to_device(W0)
+    for _ in range(3):
+        sol64.step(V, None, dt)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(fp64_steps):
+        sol64.step(V, None, dt)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = f0.elapsed_time(f1)
+    fp64_value = ws * N * 3 * fp64_steps / (fp64_ms / 1e3)
+    sol64.check()
+
+    # accuracy at t = (steps done) dt: FP32C vs FP64 vs the exact translated vortex
+    acc = None
+    if rank == 0:
+        t_fp32 = steps_done * dt
+        # bring FP64 to the same step count
+        for _ in range(steps_done - 3 - fp64_steps):
+            sol64.step(V, None, dt)
+        torch.cuda.synchronize()
+        W32 = sol.to_host(U, Ul)
+        W64 = sol64.to_host(V)
+        ex = S.cell_average(mi, lambda x, y: S.isentropic_vortex(x, y, t_fp32), order=4)
+        # cell areas from the mesh input: shoelace over the cell polygons
+        cells, cnt = mi.padded_cells()
+        P = mi.nodes[cells]
+        x, y = P[..., 0], P[..., 1]
+        a = 0.5 * np.abs((x * np.roll(y, -1, 1) - np.roll(x, -1, 1) * y).sum(1))  # padded vertex repeats add 0
+        area = a
+
+        def l1(d):
+            return float((np.abs(d[0]) * area).sum() / area.sum())
+        acc = {"t": t_fp32, "steps": steps_done, "dt": dt, "l1_rho_fp32c_vs_exact": l1(W32 - ex),
+               "l1_rho_fp64_vs_exact": l1(W64 - ex), "l1_rho_fp32c_vs_fp64": l1(W32 - W64),
+               "conservation_rel_drift_fp32c": float(np.abs(c_end - c_start).max() / np.abs(c_start).max())}
+
+    launches_per_step = 1 + 3 * ((1 if nQ else 0) + (1 if nT else 0) + 1 + (1 if nQ else 0) + (1 if nT else 0))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (compensated hi+lo state)", "data": "synthetic",
+            "config": {"workload": workload_name(args.n), "cells": N, "quads": nQ, "triangles": nT,
+                       "faces": int(mesh.info.n_faces), "precision": "fp32c", "dt": dt,
+                       "l2": "inputs larger than L2 (tables ~2.5 GB, state 128 MB per copy)",
+                       "launch": sol.launch_config().tolist(), "setup_s": round(t_setup, 1),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "steps": e2e_steps},
+            "roofline": {"kernel": "k_reconstruct (quad + triangle launches of one pass)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": f"{peak_kind} HBM copy bandwidth", "traffic": None,
+                         "algorithmic_bytes_per_launch": kbytes, "ms_per_launch": k_ms},
+            "kernel_ms": {"reconstruct": k_ms, "face": face_ms, "gather": gather_ms},
+            "fp64": {"value": fp64_value, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64_ms / fp64_steps,
+                     "fp32c_over_fp64": value / fp64_value},
+            "accuracy": acc,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * weno3.h - C ABI of the GB300 library for the third-order WENO finite-volume
+ * residual on unstructured quadrilateral / triangular / mixed meshes
+ * (Zhao, Pan, Wang: "Weighted essentially non-oscillatory scheme on
+ * unstructured quadrilateral and triangular meshes for hyperbolic
+ * conservation laws", arXiv 1712.08317).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   u_t + div F(u) = 0 on a polygon mesh (Section 2, Eq. 1 for Euler; scalar
+ *   linear advection as the scalar case), semi-discrete FV form
+ *   dW_i/dt = L(W) (Eq. 4), edge integrals by 2-point Gauss quadrature (Eq. 5),
+ *   third-order TVD Runge-Kutta in time (Section 4).
+ *
+ *   weno_mesh_create   nodes + cells -> faces, stencils (Sections 3.1, 3.2)
+ *   weno_solver_create mesh + params -> least-squares reconstruction tables
+ *                      and optimised linear weights (Sections 3.1-3.3), FP64,
+ *                      uploaded to the GPU in the solver's precision
+ *   weno_residual      R = L(U) (Eq. 4 with the WENO values of Section 3.4)
+ *   weno_step          one SSP-RK3 step in place (Section 4)
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a weno_status (0 = WENO_OK); nothing aborts or traps.
+ *    weno_last_error() gives a thread-local message for the last failure.
+ *  - Host arrays passed in are read during the call and never retained.
+ *  - The library owns its meshes, solvers, device tables and scratch memory;
+ *    the caller owns the state arrays U / U_lo / R (device memory).
+ *  - State layout: cell-major, U[cell * n_v + v] for the internal cell order
+ *    (weno_mesh_cell_permutation maps internal -> input ids). n_v = 1 for
+ *    scalar advection, 4 for Euler with W = (rho, rho u, rho v, rho E).
+ *    FP64 solvers take double arrays.  FP32C solvers take float U (the
+ *    rounded state) plus float U_lo (its compensation; U + U_lo is the
+ *    state), and produce a float residual.
+ *  - cuda_stream arguments are cudaStream_t values passed as void*
+ *    (NULL = legacy default stream).  Calls are stream-ordered and
+ *    asynchronous unless documented as synchronising.
+ */
+#ifndef WENO3_H
+#define WENO3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct weno_mesh_s* weno_mesh_t;
+typedef struct weno_solver_s* weno_solver_t;
+
+typedef enum {
+  WENO_OK = 0,
+  WENO_EINVAL = -1,    /* bad argument (null pointer, out-of-range value)           */
+  WENO_EMESH = -2,     /* cell with != 3/4 nodes, zero-area, non-convex, non-manifold */
+  WENO_EPERIODIC = -3, /* a periodic boundary face without a translated partner     */
+  WENO_ENOMEM = -4,    /* host or device allocation failed                          */
+  WENO_ECUDA = -5,     /* a CUDA runtime call failed (message in weno_last_error)   */
+  WENO_ENONPHYS = -6,  /* rho <= 0, p <= 0 or a non-finite value seen at a Gauss point */
+  WENO_ETIMEOUT = -7   /* reserved: a bounded device wait gave up                   */
+} weno_status;
+
+typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_OUTFLOW = 1 } weno_bc_kind;
+typedef enum { WENO_EQN_SCALAR = 0, WENO_EQN_EULER = 1 } weno_eqn_kind;
+typedef enum { WENO_FP64 = 0, WENO_FP32C = 1 } weno_precision;
+
+/* Boundary description of one mesh instance. */
+typedef struct {
+  int32_t bc;        /* weno_bc_kind: periodic in x and y, or outflow on every boundary face */
+  double origin[2];  /* periodic box origin (ignored for outflow)                            */
+  double extent[2];  /* periodic box size = the periods (ignored for outflow)                */
+} weno_mesh_opts;
+
+/* Scheme parameters (defaults: weno_params_default). */
+typedef struct {
+  int32_t eqn;        /* weno_eqn_kind                                                     */
+  int32_t precision;  /* weno_precision                                                    */
+  double gas_gamma;   /* specific heat ratio of Eq. 1 (Euler)                              */
+  double adv[2];      /* advection velocity (scalar)                                       */
+  double eps;         /* epsilon of the nonlinear weights, Section 3.4 (not given: 1e-6)   */
+  double theta;       /* splitting parameter of Section 3.4 (3)                            */
+  double rcond;       /* relative singular-value cut of the minimum-norm least squares that
+                         stand for the zeta-regularised solves of Eqs. 12 and 15 (1e-12)   */
+  int32_t optimize;   /* 1: optimised linear weights of Section 3.3 (default), 0: raw      */
+  int32_t linear;     /* 1: linear scheme R = sum gamma_j P^1_j (Eq. 14), 0: WENO          */
+  int32_t n_threads;  /* host threads for the precompute (0 = all hardware threads)        */
+} weno_params;
+
+typedef struct {
+  int64_t n_cells;      /* all cells (internal order: quads first, then triangles)   */
+  int64_t n_quads;      /* internal ids [0, n_quads) are quads                        */
+  int64_t n_tris;       /* internal ids [n_quads, n_cells) are triangles              */
+  int64_t n_faces;      /* faces (periodic pairs counted once; outflow faces once)    */
+  int64_t n_boundary;   /* outflow boundary faces                                     */
+  int32_t n_instances;  /* 1, or the number of meshes joined by weno_mesh_concat      */
+  int32_t reserved;
+} weno_mesh_info;
+
+/* Fills *p with the defaults: Euler, FP64, gamma 1.4, adv (1,1), eps 1e-6,
+ * theta 3, rcond 1e-12, optimize 1, linear 0, n_threads 0. */
+void weno_params_default(weno_params* p);
+
+/* Builds a mesh (Section 2; stencils of Sections 3.1 and 3.2).
+ * node_xy   [n_nodes][2] coordinates.
+ * cell_ptr  [n_cells + 1] offsets into cell_nodes; cells have 3 or 4 nodes,
+ *           either orientation (clockwise cells are reversed).
+ * cell_nodes node ids.
+ * opts      boundary description.
+ * Cells are renumbered: quads first, then triangles, each in Morton order
+ * of their centroids.  Errors: WENO_EINVAL, WENO_EMESH, WENO_EPERIODIC,
+ * WENO_ENOMEM.  Synchronous, host only (no CUDA calls). */
+int weno_mesh_create(const double* node_xy, int64_t n_nodes, const int64_t* cell_ptr,
+                     const int64_t* cell_nodes, int64_t n_cells, const weno_mesh_opts* opts,
+                     weno_mesh_t* out);
+
+/* Joins independent meshes into one batched mesh: a flattened cell / face
+ * index space with per-instance offsets.  Instance k keeps its own
+ * boundary conditions; its input ids are offset by the input cell counts of
+ * instances 0..k-1.  The inputs stay valid and owned by the caller. */
+int weno_mesh_concat(const weno_mesh_t* meshes, int32_t n, weno_mesh_t* out);
+
+int weno_mesh_get_info(weno_mesh_t mesh, weno_mesh_info* info);
+
+/* perm[internal id] = input id, n_cells entries. */
+int weno_mesh_cell_permutation(weno_mesh_t mesh, int64_t* perm);
+
+/* instance[internal id] = instance index, n_cells entries (int32). */
+int weno_mesh_cell_instance(weno_mesh_t mesh, int32_t* instance);
+
+/* Diagnostics of the linear weights (Section 3.3, Tables 1 and 2): for every
+ * cell the maximum |gamma| over its Gauss points and candidates before
+ * (raw) and after (opt) the optimisation.  Both [n_cells] in internal order.
+ * Runs the FP64 precompute on the host; synchronous. */
+int weno_mesh_weight_stats(weno_mesh_t mesh, const weno_params* params, double* max_raw, double* max_opt);
+
+void weno_mesh_destroy(weno_mesh_t mesh);
+
+/* Creates a solver on the current CUDA device: runs the FP64 precompute
+ * (least squares, candidates, linear weights and their optimisation) on the
+ * host and uploads the run-time tables in the solver's precision.  The mesh
+ * may be destroyed afterwards.  Synchronous. */
+int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_stream, weno_solver_t* out);
+
+int weno_solver_get_info(weno_solver_t s, weno_mesh_info* info);
+
+/* R = L(U) (Eq. 4).  U, U_lo, R: device arrays [n_cells * n_v] (U_lo only
+ * for FP32C, else NULL).  Stream-ordered. */
+int weno_residual(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream);
+
+/* One SSP-RK3 step (Section 4) of size dt in place on U (and U_lo). Uses a
+ * CUDA graph of the three stages, built on first use for these pointers.
+ * Stream-ordered. */
+int weno_step(weno_solver_t s, void* U, void* U_lo, double dt, void* cuda_stream);
+
+/* Same with one dt per instance: dt_dev is a device array [n_instances] of
+ * double, read when the step runs. */
+int weno_step_instances(weno_solver_t s, void* U, void* U_lo, const double* dt_dev, void* cuda_stream);
+
+/* Largest stable dt (reading of the CFL rule: dt = cfl * min_i 2|Omega_i| /
+ * sum_p (|v_i . n_p| + c_i) |l_p|, c = 0 for scalar advection), per
+ * instance: dt_out[n_instances] on the host.  Synchronising. */
+int weno_max_dt(weno_solver_t s, const void* U, const void* U_lo, double cfl, double* dt_out, void* cuda_stream);
+
+/* sum_i |Omega_i| (U + U_lo)_i in FP64 per instance and variable:
+ * sums[n_instances * n_v] on the host.  Deterministic order. Synchronising. */
+int weno_conservation(weno_solver_t s, const void* U, const void* U_lo, double* sums, void* cuda_stream);
+
+/* Reads and clears the device non-physical-state flag raised by residual /
+ * step launches: WENO_ENONPHYS if any Gauss point had rho <= 0, p <= 0 or a
+ * non-finite value since the last check.  Synchronising. */
+int weno_check(weno_solver_t s, void* cuda_stream);
+
+/* Launches one pass of the residual on its own (profiling aid; the kernels
+ * are the ones weno_residual and weno_step run):
+ *   pass 1: cell reconstruction of U (U_lo) into the solver's Gauss-point scratch
+ *           (Sections 3.1-3.4);
+ *   pass 2: face fluxes from that scratch into the solver's flux scratch (Eqs. 5-6);
+ *   pass 3: signed gather of the face fluxes into the solver's stage buffer (Eq. 4).
+ * U / U_lo are used by pass 1 only.  Stream-ordered. */
+int weno_pass(weno_solver_t s, int32_t pass, const void* U, const void* U_lo, void* cuda_stream);
+
+/* Times each kernel over a set of block sizes and grid sizes (cells per
+ * thread) on this mesh and keeps the fastest; rebuilds the step graphs.
+ * Does not modify U / U_lo.  Synchronising. */
+int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_stream);
+
+/* Current launch configuration: cfg[6] = {cell block, cell grid, face block,
+ * face grid, gather block, gather grid}. */
+int weno_solver_launch_config(weno_solver_t s, int32_t* cfg);
+
+void weno_solver_destroy(weno_solver_t s);
+
+const char* weno_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WENO3_H */

@@ -1,0 +1,406 @@
+// sm_103a kernels of the WENO3 residual and the SSP-RK3 stage update.
+//
+//   k_reconstruct  one thread per (cell, variable): candidate gradients from
+//                  gathered stencil averages, smoothness indicators, split
+//                  linear weights, new indicator, nonlinear weights and the
+//                  Gauss-point values (Sections 3.1-3.4).
+//   k_face         one thread per face: two Gauss points, rotated HLLC
+//                  (Euler) or upwind (scalar) flux, |l|/2 (F1 + F2) (Eqs. 5-6).
+//   k_gather       one thread per cell: signed gather of its face fluxes
+//                  (Eq. 4, no atomics) fused with the RK3 stage (Section 4).
+//
+// Layouts: state U[cell][v] (cell-major), Gauss values Wg[point][v] with the
+// points of a quad at 8q..8q+7 and of a triangle at 8 nQ + 6t.., face fluxes
+// F[face][v]; per-cell tables are structure-of-arrays with the cell index
+// fastest, so the 4 variable threads of a cell share each table sector.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace weno {
+namespace dev {
+
+// Candidate sub-stencils S_j = {i0, a, b} (Sections 3.1 and 3.2).
+template <int M> struct Sub;
+template <> struct Sub<12> {
+  static __device__ __forceinline__ int a(int j) { constexpr int t[12] = {1, 2, 3, 4, 1, 1, 3, 3, 4, 2, 2, 4}; return t[j]; }
+  static __device__ __forceinline__ int b(int j) { constexpr int t[12] = {2, 3, 4, 1, 5, 6, 7, 8, 9, 10, 11, 12}; return t[j]; }
+};
+template <> struct Sub<9> {
+  static __device__ __forceinline__ int a(int j) { constexpr int t[9] = {1, 2, 3, 1, 2, 3, 3, 1, 2}; return t[j]; }
+  static __device__ __forceinline__ int b(int j) { constexpr int t[9] = {2, 3, 1, 4, 5, 6, 7, 8, 9}; return t[j]; }
+};
+
+template <typename T> __device__ __forceinline__ T fabs_(T x) { return x < T(0) ? -x : x; }
+
+// Error-free sum (Knuth TwoSum): s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// ---------------------------------------------------------------- K1
+// Threads t in [0, N*NV): cell q = t / NV of the group, variable v = t % NV.
+template <typename T, int NV, int M, int G, bool COMP>
+__global__ void __launch_bounds__(256) k_reconstruct(
+    const T* __restrict__ U, const T* __restrict__ Ulo, const int32_t* __restrict__ slot,
+    const T* __restrict__ gop, const T* __restrict__ dg, const T* __restrict__ gam,
+    const T* __restrict__ area, int64_t N, int64_t first, int64_t gbase, T* __restrict__ Wg,
+    T eps, T theta, int linear) {
+  const int64_t total = N * NV;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / NV;
+    const int v = (int)(t - q * NV);
+    const int64_t c = first + q;
+    const T w0 = __ldg(U + c * NV + v);
+    const T l0 = COMP ? __ldg(Ulo + c * NV + v) : T(0);
+    // differences to the stencil cells (slots 1..M), replacements already resolved
+    T dW[M + 1];
+    dW[0] = T(0);
+#pragma unroll
+    for (int s = 1; s <= M; ++s) {
+      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
+      T d = __ldg(U + cs * NV + v) - w0;
+      if (COMP) d += __ldg(Ulo + cs * NV + v) - l0;
+      dW[s] = d;
+    }
+    // candidate gradients g_j = D_j^+ (dW_a, dW_b), beta_j = |Omega| |g_j|^2
+    T gx[M], gy[M], beta[M];
+    const T a0 = __ldg(area + c);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const T da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
+      const T m0 = __ldg(gop + (int64_t)(j * 4 + 0) * N + q), m1 = __ldg(gop + (int64_t)(j * 4 + 1) * N + q);
+      const T m2 = __ldg(gop + (int64_t)(j * 4 + 2) * N + q), m3 = __ldg(gop + (int64_t)(j * 4 + 3) * N + q);
+      gx[j] = m0 * da + m1 * db;
+      gy[j] = m2 * da + m3 * db;
+      beta[j] = a0 * (gx[j] * gx[j] + gy[j] * gy[j]);
+    }
+    T* out = Wg + (gbase + q * G) * NV + v;
+#pragma unroll 1
+    for (int g = 0; g < G; ++g) {
+      const T dx = __ldg(dg + (int64_t)(g * 2) * N + q), dy = __ldg(dg + (int64_t)(g * 2 + 1) * N + q);
+      const T* gg = gam + (int64_t)(g * M) * N + q;
+      T incr;
+      if (linear) {
+        incr = T(0);
+#pragma unroll
+        for (int j = 0; j < M; ++j) incr += __ldg(gg + (int64_t)j * N) * (gx[j] * dx + gy[j] * dy);
+      } else {
+        // splitting of Section 3.4: gt+ = (gamma + theta |gamma|)/2, gt- = gt+ - gamma
+        T sp = T(0), sm = T(0);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          const T gj = __ldg(gg + (int64_t)j * N);
+          const T tp = T(0.5) * (gj + theta * fabs_(gj));
+          sp += tp;
+          sm += tp - gj;
+        }
+        const T isp = T(1) / sp, ism = T(1) / sm;
+        T Ap = T(0), Bp = T(0), Am = T(0), Bm = T(0);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          const T gj = __ldg(gg + (int64_t)j * N);
+          const T tp = T(0.5) * (gj + theta * fabs_(gj));
+          const T gp = tp * isp, gm = (tp - gj) * ism;
+          const T p = gx[j] * dx + gy[j] * dy;  // P^1_j(x_G) - W0
+          const T qp = gp * beta[j], qm = gm * beta[j];
+          const T bp = beta[j] * (T(1) + qp + qp * qp) + eps;  // new indicator + eps
+          const T bm = beta[j] * (T(1) + qm + qm * qm) + eps;
+          const T ap = gp / (bp * bp), am = gm / (bm * bm);
+          Ap += ap;
+          Bp += ap * p;
+          Am += am;
+          Bm += am * p;
+        }
+        // R - W0 = sigma+ sum delta+ p - sigma- sum delta- p
+        incr = sp * (Bp / Ap) - sm * (Bm / Am);
+      }
+      out[(int64_t)g * NV] = COMP ? w0 + (l0 + incr) : w0 + incr;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K2
+template <typename T>
+struct Prm { T gas_gamma, ax, ay; };
+
+template <typename T>
+__device__ __forceinline__ void euler_x_flux(T r, T un, T ut, T E, T p, T f[4]) {
+  f[0] = r * un;
+  f[1] = r * un * un + p;
+  f[2] = r * un * ut;
+  f[3] = (E + p) * un;
+}
+
+// HLLC in the frame of the unit normal (nx, ny); returns the flux rotated back.
+template <typename T>
+__device__ __forceinline__ void hllc(const T wl[4], const T wr[4], T nx, T ny, T gam, T out[4], bool& bad) {
+  const T rl = wl[0], rr = wr[0];
+  const T irl = T(1) / rl, irr = T(1) / rr;
+  const T ul = (wl[1] * nx + wl[2] * ny) * irl, vl = (wl[2] * nx - wl[1] * ny) * irl;
+  const T ur = (wr[1] * nx + wr[2] * ny) * irr, vr = (wr[2] * nx - wr[1] * ny) * irr;
+  const T pl = (gam - T(1)) * (wl[3] - T(0.5) * rl * (ul * ul + vl * vl));
+  const T pr = (gam - T(1)) * (wr[3] - T(0.5) * rr * (ur * ur + vr * vr));
+  bad |= !(rl > T(0)) || !(rr > T(0)) || !(pl > T(0)) || !(pr > T(0)) || !(wl[3] == wl[3]) || !(wr[3] == wr[3]);
+  const T cl = sqrt(gam * pl * irl), cr = sqrt(gam * pr * irr);
+  // Roe averages
+  const T sl = sqrt(rl), sr = sqrt(rr), iw = T(1) / (sl + sr);
+  const T ua = (sl * ul + sr * ur) * iw, va = (sl * vl + sr * vr) * iw;
+  const T Hl = (wl[3] + pl) * irl, Hr = (wr[3] + pr) * irr;
+  const T Ha = (sl * Hl + sr * Hr) * iw;
+  const T ca = sqrt((gam - T(1)) * (Ha - T(0.5) * (ua * ua + va * va)));
+  const T SL = fmin(ul - cl, ua - ca), SR = fmax(ur + cr, ua + ca);
+  const T ml = rl * (SL - ul), mr = rr * (SR - ur);
+  const T SS = (pr - pl + ul * ml - ur * mr) / (ml - mr);
+  T f[4];
+  if (SL >= T(0)) {
+    euler_x_flux(rl, ul, vl, wl[3], pl, f);
+  } else if (SS >= T(0)) {
+    euler_x_flux(rl, ul, vl, wl[3], pl, f);
+    const T k = ml / (SL - SS);  // rho* of the left star state
+    const T Es = k * (wl[3] * irl + (SS - ul) * (SS + pl / ml));
+    f[0] += SL * (k - rl);
+    f[1] += SL * (k * SS - rl * ul);
+    f[2] += SL * (k * vl - rl * vl);
+    f[3] += SL * (Es - wl[3]);
+  } else if (SR > T(0)) {
+    euler_x_flux(rr, ur, vr, wr[3], pr, f);
+    const T k = mr / (SR - SS);
+    const T Es = k * (wr[3] * irr + (SS - ur) * (SS + pr / mr));
+    f[0] += SR * (k - rr);
+    f[1] += SR * (k * SS - rr * ur);
+    f[2] += SR * (k * vr - rr * vr);
+    f[3] += SR * (Es - wr[3]);
+  } else {
+    euler_x_flux(rr, ur, vr, wr[3], pr, f);
+  }
+  out[0] = f[0];
+  out[1] = f[1] * nx - f[2] * ny;
+  out[2] = f[1] * ny + f[2] * nx;
+  out[3] = f[3];
+}
+
+template <typename T, int NV>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, T w[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) w[v] = __ldg(p + v);
+}
+template <>
+__device__ __forceinline__ void load_vec<float, 4>(const float* __restrict__ p, float w[4]) {
+  const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+  w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+}
+template <>
+__device__ __forceinline__ void load_vec<double, 4>(const double* __restrict__ p, double w[4]) {
+  const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 y = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  w[0] = x.x; w[1] = x.y; w[2] = y.x; w[3] = y.y;
+}
+template <typename T, int NV>
+__device__ __forceinline__ void store_vec(T* p, const T w[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) p[v] = w[v];
+}
+template <>
+__device__ __forceinline__ void store_vec<float, 4>(float* p, const float w[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
+}
+template <>
+__device__ __forceinline__ void store_vec<double, 4>(double* p, const double w[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(w[0], w[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(w[2], w[3]);
+}
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_face(
+    const T* __restrict__ Wg, const int32_t* __restrict__ gl, const int32_t* __restrict__ gr,
+    const T* __restrict__ fnx, const T* __restrict__ fny, const T* __restrict__ flen, int64_t nF,
+    T* __restrict__ F, Prm<T> prm, int* __restrict__ flag) {
+  bool bad = false;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nF; f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t il = __ldg(gl + f);
+    const int64_t ir = __ldg(gr + f);
+    const T nx = __ldg(fnx + f), ny = __ldg(fny + f), len = __ldg(flen + f);
+    T acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = T(0);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      T wl[NV], wr[NV], fk[NV];
+      load_vec<T, NV>(Wg + (il + k) * NV, wl);
+      // the right cell meets the left cell's point k at its point 1 - k
+      if (ir >= 0) load_vec<T, NV>(Wg + (ir + 1 - k) * NV, wr);
+      else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) wr[v] = wl[v];
+      }
+      if (NV == 4) {
+        hllc<T>(wl, wr, nx, ny, prm.gas_gamma, fk, bad);
+      } else {
+        const T an = prm.ax * nx + prm.ay * ny;
+        fk[0] = an * (an >= T(0) ? wl[0] : wr[0]);
+        bad |= !(fk[0] == fk[0]);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += fk[v];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] *= T(0.5) * len;
+    store_vec<T, NV>(F + f * NV, acc);
+  }
+  if (bad) *flag = 1;  // every writer stores the same value
+}
+
+// ---------------------------------------------------------------- K3
+// MODE 0: R = L(U).  MODE 1..3: SSP-RK3 stage s written as
+//   W(s) = W^n + c_s ((W(s-1) - W^n) + dt L(W(s-1))), c = 1, 1/4, 2/3, W(0) = W^n,
+// i.e. the stages of Section 4 with the combination regrouped around W^n.
+// Stages 1, 2 write the stage buffer Ws; stage 3 writes U (= W^{n+1}).
+template <typename T, int NV, int NFACE, bool COMP, int MODE>
+__global__ void __launch_bounds__(256) k_gather(
+    const T* __restrict__ F, const int32_t* __restrict__ cf, const T* __restrict__ inv_area, int64_t N,
+    int64_t first, T* __restrict__ U, T* __restrict__ Ulo, T* __restrict__ Ws, T* __restrict__ Wslo,
+    T* __restrict__ R, const double* __restrict__ dt, const int32_t* __restrict__ inst) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = first + q;
+    T acc[NV], comp[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc[v] = T(0); comp[v] = T(0); }
+#pragma unroll
+    for (int k = 0; k < NFACE; ++k) {
+      const int32_t e = __ldg(cf + (int64_t)k * N + q);
+      const int64_t f = e >= 0 ? e : ~e;
+      T fv[NV];
+      load_vec<T, NV>(F + f * NV, fv);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T x = e >= 0 ? -fv[v] : fv[v];  // outward flux leaves the L cell
+        if (COMP) {  // Kahan-compensated accumulation
+          const T y = x - comp[v];
+          const T s = acc[v] + y;
+          comp[v] = (s - acc[v]) - y;
+          acc[v] = s;
+        } else {
+          acc[v] += x;
+        }
+      }
+    }
+    const T ia = __ldg(inv_area + c);
+    T res[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) res[v] = acc[v] * ia;
+    if (MODE == 0) {
+      store_vec<T, NV>(R + c * NV, res);
+    } else {
+      const double dtd = dt[inst ? __ldg(inst + c) : 0];
+      const T h = (T)dtd;
+      const T cs = MODE == 1 ? T(1) : (MODE == 2 ? T(0.25) : T(2.0 / 3.0));
+      T un[NV], ws[NV], out[NV];
+      load_vec<T, NV>(U + c * NV, un);
+      if (MODE > 1) load_vec<T, NV>(Ws + c * NV, ws);
+      if (!COMP) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T d = (MODE > 1 ? ws[v] - un[v] : T(0)) + h * res[v];
+          out[v] = un[v] + cs * d;
+        }
+        store_vec<T, NV>(MODE == 3 ? U + c * NV : Ws + c * NV, out);
+      } else {
+        T unl[NV], wsl[NV], outl[NV];
+        load_vec<T, NV>(Ulo + c * NV, unl);
+        if (MODE > 1) load_vec<T, NV>(Wslo + c * NV, wsl);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          // increment from W^n, small: plain FP32 is enough for it
+          const T d = (MODE > 1 ? (ws[v] - un[v]) + (wsl[v] - unl[v]) : T(0)) + h * res[v];
+          const float inc = (float)(cs * d);
+          float s, e;
+          two_sum((float)un[v], inc, s, e);
+          const float lo = __fadd_rn((float)unl[v], e);
+          const float hi = __fadd_rn(s, lo);           // renormalise (fast two-sum)
+          out[v] = hi;
+          outl[v] = __fsub_rn(lo, __fsub_rn(hi, s));
+        }
+        store_vec<T, NV>(MODE == 3 ? U + c * NV : Ws + c * NV, out);
+        store_vec<T, NV>(MODE == 3 ? Ulo + c * NV : Wslo + c * NV, outl);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K4 (reductions, not on the hot path)
+// Per-cell stable step 2|Omega| / sum_p (|v.n_p| + c)|l_p| (FP64).
+template <typename T, int NV, int NFACE, bool COMP>
+__global__ void k_cell_dt(const T* __restrict__ U, const T* __restrict__ Ulo, const int32_t* __restrict__ cf,
+                          const double* __restrict__ fnx, const double* __restrict__ fny,
+                          const double* __restrict__ flen, const double* __restrict__ area, int64_t N,
+                          int64_t first, double gas_gamma, double ax, double ay, double* __restrict__ out) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = first + q;
+    double w[NV];
+    for (int v = 0; v < NV; ++v) w[v] = (double)U[c * NV + v] + (COMP ? (double)Ulo[c * NV + v] : 0.0);
+    double u = ax, vv = ay, snd = 0.0;
+    if (NV == 4) {
+      u = w[1] / w[0];
+      vv = w[2] / w[0];
+      const double p = (gas_gamma - 1.0) * (w[3] - 0.5 * w[0] * (u * u + vv * vv));
+      snd = sqrt(gas_gamma * p / w[0]);
+    }
+    double s = 0.0;
+    for (int k = 0; k < NFACE; ++k) {
+      const int32_t e = cf[(int64_t)k * N + q];
+      const int64_t f = e >= 0 ? e : ~e;
+      s += (fabs(u * fnx[f] + vv * fny[f]) + snd) * flen[f];
+    }
+    out[c] = 2.0 * area[c] / s;
+  }
+}
+
+// One block per instance: deterministic min / sums over the instance's quad
+// range [q0, q1) and triangle range [t0, t1).  mode 0: min of x[c];
+// mode 1: sums of area[c] * (U + U_lo)[c][v] for every v.
+template <typename T, int NV, bool COMP>
+__global__ void k_instance_reduce(const double* __restrict__ x, const T* __restrict__ U, const T* __restrict__ Ulo,
+                                  const double* __restrict__ area, const int64_t* __restrict__ ranges, int mode,
+                                  double* __restrict__ out) {
+  __shared__ double sh[256 * NV];
+  const int inst = blockIdx.x;
+  const int64_t r[4] = {ranges[4 * inst], ranges[4 * inst + 1], ranges[4 * inst + 2], ranges[4 * inst + 3]};
+  double acc[NV];
+  for (int v = 0; v < NV; ++v) acc[v] = mode == 0 ? 1e300 : 0.0;
+  for (int part = 0; part < 2; ++part) {
+    for (int64_t c = r[2 * part] + threadIdx.x; c < r[2 * part + 1]; c += blockDim.x) {
+      if (mode == 0) {
+        acc[0] = fmin(acc[0], x[c]);
+      } else {
+        for (int v = 0; v < NV; ++v)
+          acc[v] += area[c] * ((double)U[c * NV + v] + (COMP ? (double)Ulo[c * NV + v] : 0.0));
+      }
+    }
+  }
+  for (int v = 0; v < NV; ++v) sh[v * 256 + threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int v = 0; v < NV; ++v) {
+        const double a = sh[v * 256 + threadIdx.x], b = sh[v * 256 + threadIdx.x + s];
+        sh[v * 256 + threadIdx.x] = mode == 0 ? fmin(a, b) : a + b;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (mode == 0) out[inst] = sh[0];
+    else for (int v = 0; v < NV; ++v) out[inst * NV + v] = sh[v * 256];
+  }
+}
+
+__global__ void k_fill(double* __restrict__ p, double v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+}  // namespace dev
+}  // namespace weno

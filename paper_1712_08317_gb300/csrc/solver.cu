@@ -1,0 +1,678 @@
+// C ABI of the library: meshes (host), solvers (device tables, launches,
+// CUDA graphs of the RK3 step, autotuning, reductions).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "host_lsq.hpp"
+#include "host_mesh.hpp"
+#include "kernels.cuh"
+#include "weno3.h"
+
+using weno::GroupTables;
+using weno::Mesh;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(WENO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+struct Launch {
+  int block = 256;
+  int grid = 0;  // 0: one thread per work item
+};
+
+unsigned grid_of(const Launch& l, int64_t work) {
+  const int64_t full = (work + l.block - 1) / l.block;
+  const int64_t g = l.grid > 0 ? std::min<int64_t>(l.grid, full) : full;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 0x7fffffff));
+}
+
+}  // namespace
+
+struct weno_mesh_s {
+  Mesh m;
+  // FP64 precompute of the last solver created on this mesh (same rcond / optimize reuse it)
+  std::shared_ptr<std::pair<GroupTables, GroupTables>> tables;
+  double tables_rcond = -1.0;
+  int tables_optimize = -1;
+};
+
+struct weno_solver_s {
+  int dev = 0, nsm = 0;
+  weno_params prm{};
+  int nv = 4;
+  bool fp64 = true;
+  size_t esz = 8;
+  int64_t nQ = 0, nT = 0, N = 0, nF = 0, n_boundary = 0;
+  int n_inst = 1;
+  // device tables
+  void *q_gop = nullptr, *q_dg = nullptr, *q_gam = nullptr, *t_gop = nullptr, *t_dg = nullptr, *t_gam = nullptr;
+  int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
+  void *area = nullptr, *inv_area = nullptr;
+  double* area64 = nullptr;
+  int32_t *gl = nullptr, *gr = nullptr;
+  void *fnx = nullptr, *fny = nullptr, *flen = nullptr;
+  double *fnx64 = nullptr, *fny64 = nullptr, *flen64 = nullptr;
+  int32_t* inst = nullptr;
+  int64_t* ranges = nullptr;
+  // scratch
+  void *Wg = nullptr, *F = nullptr, *Ws = nullptr, *Wslo = nullptr;
+  double *dt_dev = nullptr, *red = nullptr, *cell_dt = nullptr;
+  int* flag = nullptr;
+  std::vector<void*> allocs;
+  Launch k1q, k1t, k2, k3q, k3t;
+  cudaStream_t cap = nullptr;
+  struct Graph {
+    const void* U;
+    const void* Ulo;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+
+  ~weno_solver_s() {
+    DeviceGuard g(dev);
+    for (auto& x : graphs) cudaGraphExecDestroy(x.exec);
+    if (cap) cudaStreamDestroy(cap);
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename P>
+  int alloc(P** p, size_t bytes) {
+    void* q = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return fail(WENO_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(q);
+    *p = reinterpret_cast<P*>(q);
+    return WENO_OK;
+  }
+  void drop_graphs() {
+    for (auto& x : graphs) cudaGraphExecDestroy(x.exec);
+    graphs.clear();
+  }
+};
+
+namespace {
+
+using S = weno_solver_s;
+
+// ------------------------------------------------------------ launches
+// which: bit 0 = quad group, bit 1 = triangle group
+template <typename T, int NV, bool COMP>
+void launch_reconstruct(S& s, const void* U, const void* Ulo, cudaStream_t st, int which = 3) {
+  const T* u = static_cast<const T*>(U);
+  const T* ul = static_cast<const T*>(Ulo);
+  const T eps = (T)s.prm.eps, th = (T)s.prm.theta;
+  if (s.nQ && (which & 1))
+    weno::dev::k_reconstruct<T, NV, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
+        u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
+        (T*)s.Wg, eps, th, s.prm.linear);
+  if (s.nT && (which & 2))
+    weno::dev::k_reconstruct<T, NV, 9, 6, COMP><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
+        u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
+        8 * s.nQ, (T*)s.Wg, eps, th, s.prm.linear);
+}
+
+template <typename T, int NV, bool COMP>
+void launch_face(S& s, cudaStream_t st) {
+  weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
+  if (s.nF)
+    weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
+        (const T*)s.Wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)s.F, p, s.flag);
+}
+
+template <typename T, int NV, bool COMP, int MODE>
+void launch_gather_mode(S& s, void* U, void* Ulo, void* R, cudaStream_t st, int which) {
+  if (s.nQ && (which & 1))
+    weno::dev::k_gather<T, NV, 4, COMP, MODE><<<grid_of(s.k3q, s.nQ), s.k3q.block, 0, st>>>(
+        (const T*)s.F, s.q_cf, (const T*)s.inv_area, s.nQ, 0, (T*)U, (T*)Ulo, (T*)s.Ws, (T*)s.Wslo, (T*)R,
+        s.dt_dev, s.inst);
+  if (s.nT && (which & 2))
+    weno::dev::k_gather<T, NV, 3, COMP, MODE><<<grid_of(s.k3t, s.nT), s.k3t.block, 0, st>>>(
+        (const T*)s.F, s.t_cf, (const T*)s.inv_area, s.nT, s.nQ, (T*)U, (T*)Ulo, (T*)s.Ws, (T*)s.Wslo, (T*)R,
+        s.dt_dev, s.inst);
+}
+
+template <typename T, int NV, bool COMP>
+void launch_gather(S& s, int mode, void* U, void* Ulo, void* R, cudaStream_t st, int which = 3) {
+  switch (mode) {
+    case 0: launch_gather_mode<T, NV, COMP, 0>(s, U, Ulo, R, st, which); break;
+    case 1: launch_gather_mode<T, NV, COMP, 1>(s, U, Ulo, R, st, which); break;
+    case 2: launch_gather_mode<T, NV, COMP, 2>(s, U, Ulo, R, st, which); break;
+    default: launch_gather_mode<T, NV, COMP, 3>(s, U, Ulo, R, st, which); break;
+  }
+}
+
+template <typename T, int NV, bool COMP>
+void launch_step_body(S& s, void* U, void* Ulo, cudaStream_t st) {
+  for (int stage = 1; stage <= 3; ++stage) {
+    const void* src = stage == 1 ? U : s.Ws;
+    const void* srclo = stage == 1 ? Ulo : s.Wslo;
+    launch_reconstruct<T, NV, COMP>(s, src, srclo, st);
+    launch_face<T, NV, COMP>(s, st);
+    launch_gather<T, NV, COMP>(s, stage, U, Ulo, nullptr, st);
+  }
+}
+
+// one call per precision / variable count
+#define WENO_DISPATCH(s, FN, ...)                                  \
+  do {                                                             \
+    if ((s).fp64) {                                                \
+      if ((s).nv == 4) FN<double, 4, false>(__VA_ARGS__);          \
+      else FN<double, 1, false>(__VA_ARGS__);                      \
+    } else {                                                       \
+      if ((s).nv == 4) FN<float, 4, true>(__VA_ARGS__);            \
+      else FN<float, 1, true>(__VA_ARGS__);                        \
+    }                                                              \
+  } while (0)
+
+template <typename T, int NV, bool COMP>
+void launch_cell_dt(S& s, const void* U, const void* Ulo, cudaStream_t st) {
+  const T* u = (const T*)U;
+  const T* ul = (const T*)Ulo;
+  if (s.nQ)
+    weno::dev::k_cell_dt<T, NV, 4, COMP><<<(unsigned)((s.nQ + 255) / 256), 256, 0, st>>>(
+        u, ul, s.q_cf, s.fnx64, s.fny64, s.flen64, s.area64, s.nQ, 0, s.prm.gas_gamma, s.prm.adv[0], s.prm.adv[1],
+        s.cell_dt);
+  if (s.nT)
+    weno::dev::k_cell_dt<T, NV, 3, COMP><<<(unsigned)((s.nT + 255) / 256), 256, 0, st>>>(
+        u, ul, s.t_cf, s.fnx64, s.fny64, s.flen64, s.area64, s.nT, s.nQ, s.prm.gas_gamma, s.prm.adv[0],
+        s.prm.adv[1], s.cell_dt);
+}
+
+template <typename T, int NV, bool COMP>
+void launch_reduce(S& s, const void* U, const void* Ulo, int mode, cudaStream_t st) {
+  weno::dev::k_instance_reduce<T, NV, COMP><<<s.n_inst, 256, 0, st>>>(s.cell_dt, (const T*)U, (const T*)Ulo,
+                                                                       s.area64, s.ranges, mode, s.red);
+}
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(WENO_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return WENO_OK;
+}
+
+template <typename D>
+int upload(S& s, D** dst, const std::vector<D>& src, cudaStream_t st) {
+  int r = s.alloc(dst, src.size() * sizeof(D));
+  if (r) return r;
+  if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(D), cudaMemcpyHostToDevice, st));
+  return WENO_OK;
+}
+
+// Upload a double table in the solver's precision.
+int upload_real(S& s, void** dst, const std::vector<double>& src, cudaStream_t st) {
+  if (s.fp64) {
+    double* d;
+    int r = upload(s, &d, src, st);
+    *dst = d;
+    return r;
+  }
+  std::vector<float> f(src.size());
+  for (size_t i = 0; i < src.size(); ++i) f[i] = (float)src[i];
+  float* d;
+  int r = upload(s, &d, f, st);
+  if (r) return r;
+  CK(cudaStreamSynchronize(st));  // f goes out of scope
+  *dst = d;
+  return WENO_OK;
+}
+
+int capture_step(S& s, void* U, void* Ulo);
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* weno_last_error(void) { return g_err.c_str(); }
+
+void weno_params_default(weno_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eqn = WENO_EQN_EULER;
+  p->precision = WENO_FP64;
+  p->gas_gamma = 1.4;
+  p->adv[0] = 1.0;
+  p->adv[1] = 1.0;
+  p->eps = 1e-6;
+  p->theta = 3.0;
+  p->rcond = 1e-12;
+  p->optimize = 1;
+  p->linear = 0;
+  p->n_threads = 0;
+}
+
+int weno_mesh_create(const double* node_xy, int64_t n_nodes, const int64_t* cell_ptr, const int64_t* cell_nodes,
+                     int64_t n_cells, const weno_mesh_opts* opts, weno_mesh_t* out) {
+  if (!node_xy || !cell_ptr || !cell_nodes || !opts || !out) return fail(WENO_EINVAL, "null argument");
+  if (opts->bc != WENO_BC_PERIODIC && opts->bc != WENO_BC_OUTFLOW) return fail(WENO_EINVAL, "unknown boundary kind");
+  *out = nullptr;
+  try {
+    auto m = std::make_unique<weno_mesh_s>();
+    std::string err;
+    int r = weno::build_mesh(node_xy, n_nodes, cell_ptr, cell_nodes, n_cells, opts->bc, opts->origin, opts->extent,
+                             m->m, err);
+    if (r) return fail(r, err);
+    *out = m.release();
+  } catch (const std::bad_alloc&) {
+    return fail(WENO_ENOMEM, "host allocation failed while building the mesh");
+  }
+  return WENO_OK;
+}
+
+int weno_mesh_concat(const weno_mesh_t* meshes, int32_t n, weno_mesh_t* out) {
+  if (!meshes || !out || n <= 0) return fail(WENO_EINVAL, "bad arguments to weno_mesh_concat");
+  *out = nullptr;
+  try {
+    std::vector<const Mesh*> v(n);
+    for (int i = 0; i < n; ++i) {
+      if (!meshes[i]) return fail(WENO_EINVAL, "null mesh");
+      v[i] = &meshes[i]->m;
+    }
+    auto m = std::make_unique<weno_mesh_s>();
+    std::string err;
+    int r = weno::concat_meshes(v.data(), n, m->m, err);
+    if (r) return fail(r, err);
+    *out = m.release();
+  } catch (const std::bad_alloc&) {
+    return fail(WENO_ENOMEM, "host allocation failed while joining meshes");
+  }
+  return WENO_OK;
+}
+
+int weno_mesh_get_info(weno_mesh_t mesh, weno_mesh_info* info) {
+  if (!mesh || !info) return fail(WENO_EINVAL, "null argument");
+  const Mesh& m = mesh->m;
+  info->n_cells = m.n();
+  info->n_quads = m.nQ;
+  info->n_tris = m.nT;
+  info->n_faces = m.nF;
+  info->n_boundary = m.n_boundary;
+  info->n_instances = m.n_inst;
+  info->reserved = 0;
+  return WENO_OK;
+}
+
+int weno_mesh_cell_permutation(weno_mesh_t mesh, int64_t* perm) {
+  if (!mesh || !perm) return fail(WENO_EINVAL, "null argument");
+  std::copy(mesh->m.perm.begin(), mesh->m.perm.end(), perm);
+  return WENO_OK;
+}
+
+int weno_mesh_cell_instance(weno_mesh_t mesh, int32_t* instance) {
+  if (!mesh || !instance) return fail(WENO_EINVAL, "null argument");
+  std::copy(mesh->m.inst.begin(), mesh->m.inst.end(), instance);
+  return WENO_OK;
+}
+
+int weno_mesh_weight_stats(weno_mesh_t mesh, const weno_params* params, double* max_raw, double* max_opt) {
+  if (!mesh || !max_raw || !max_opt) return fail(WENO_EINVAL, "null argument");
+  weno_params p;
+  if (params) p = *params;
+  else weno_params_default(&p);
+  weno::LsqParams lp;
+  lp.rcond = p.rcond > 0 ? p.rcond : 1e-12;
+  lp.optimize = p.optimize != 0;
+  lp.n_threads = p.n_threads;
+  try {
+    GroupTables tq, tt;
+    std::string err;
+    int r = weno::precompute_tables(mesh->m, lp, tq, tt, err);
+    if (r) return fail(r, err);
+    for (int64_t i = 0; i < tq.N; ++i) { max_raw[i] = tq.max_raw[i]; max_opt[i] = tq.max_opt[i]; }
+    for (int64_t i = 0; i < tt.N; ++i) { max_raw[tq.N + i] = tt.max_raw[i]; max_opt[tq.N + i] = tt.max_opt[i]; }
+  } catch (const std::bad_alloc&) {
+    return fail(WENO_ENOMEM, "host allocation failed in the precompute");
+  }
+  return WENO_OK;
+}
+
+void weno_mesh_destroy(weno_mesh_t mesh) { delete mesh; }
+
+int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_stream, weno_solver_t* out) {
+  if (!mesh || !params || !out) return fail(WENO_EINVAL, "null argument");
+  *out = nullptr;
+  const weno_params& p = *params;
+  if (p.eqn != WENO_EQN_SCALAR && p.eqn != WENO_EQN_EULER) return fail(WENO_EINVAL, "unknown equation");
+  if (p.precision != WENO_FP64 && p.precision != WENO_FP32C) return fail(WENO_EINVAL, "unknown precision");
+  if (!(p.eps > 0) || !(p.theta >= 1) || (p.eqn == WENO_EQN_EULER && !(p.gas_gamma > 1)))
+    return fail(WENO_EINVAL, "parameters out of range (eps > 0, theta >= 1, gamma > 1)");
+  const Mesh& m = mesh->m;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::unique_ptr<S> s;
+  try {
+    s.reset(new S());
+  } catch (const std::bad_alloc&) {
+    return fail(WENO_ENOMEM, "host allocation failed");
+  }
+  CK(cudaGetDevice(&s->dev));
+  CK(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
+  s->prm = p;
+  if (!(s->prm.rcond > 0)) s->prm.rcond = 1e-12;
+  s->nv = p.eqn == WENO_EQN_EULER ? 4 : 1;
+  s->fp64 = p.precision == WENO_FP64;
+  s->esz = s->fp64 ? 8 : 4;
+  s->nQ = m.nQ;
+  s->nT = m.nT;
+  s->N = m.n();
+  s->nF = m.nF;
+  s->n_boundary = m.n_boundary;
+  s->n_inst = m.n_inst;
+  // precompute on the host (FP64), shared by solvers of the same mesh and weight options
+  if (!mesh->tables || mesh->tables_rcond != s->prm.rcond || mesh->tables_optimize != (p.optimize != 0)) {
+    try {
+      mesh->tables.reset();
+      auto tab = std::make_shared<std::pair<GroupTables, GroupTables>>();
+      weno::LsqParams lp;
+      lp.rcond = s->prm.rcond;
+      lp.optimize = p.optimize != 0;
+      lp.n_threads = p.n_threads;
+      std::string err;
+      int r = weno::precompute_tables(m, lp, tab->first, tab->second, err);
+      if (r) return fail(r, err);
+      mesh->tables = tab;
+      mesh->tables_rcond = s->prm.rcond;
+      mesh->tables_optimize = p.optimize != 0;
+    } catch (const std::bad_alloc&) {
+      return fail(WENO_ENOMEM, "host allocation failed in the precompute");
+    }
+  }
+  const GroupTables& tq = mesh->tables->first;
+  const GroupTables& tt = mesh->tables->second;
+  S& d = *s;
+  int r;
+  if ((r = upload(d, &d.q_slot, tq.slot, st))) return r;
+  if ((r = upload(d, &d.t_slot, tt.slot, st))) return r;
+  if ((r = upload_real(d, &d.q_gop, tq.gop, st))) return r;
+  if ((r = upload_real(d, &d.q_dg, tq.dg, st))) return r;
+  if ((r = upload_real(d, &d.q_gam, tq.gam, st))) return r;
+  if ((r = upload_real(d, &d.t_gop, tt.gop, st))) return r;
+  if ((r = upload_real(d, &d.t_dg, tt.dg, st))) return r;
+  if ((r = upload_real(d, &d.t_gam, tt.gam, st))) return r;
+  {
+    std::vector<double> inv(d.N);
+    for (int64_t c = 0; c < d.N; ++c) inv[c] = 1.0 / m.area[c];
+    if ((r = upload_real(d, &d.area, m.area, st))) return r;
+    if ((r = upload_real(d, &d.inv_area, inv, st))) return r;
+    if ((r = upload(d, &d.area64, m.area, st))) return r;
+    CK(cudaStreamSynchronize(st));
+  }
+  {
+    // cell -> face lists with orientation (f: cell is L, ~f: cell is R)
+    std::vector<int32_t> cq((size_t)4 * d.nQ), ct((size_t)3 * d.nT);
+    for (int64_t c = 0; c < d.N; ++c) {
+      const int nf = m.nvert[c];
+      for (int k = 0; k < nf; ++k) {
+        const int32_t f = m.cell_face[c * 4 + k];
+        const bool left = m.fL[f] == (int32_t)c && m.fkL[f] == k;
+        const int32_t e = left ? f : ~f;
+        if (c < d.nQ) cq[(size_t)k * d.nQ + c] = e;
+        else ct[(size_t)k * d.nT + (c - d.nQ)] = e;
+      }
+    }
+    if ((r = upload(d, &d.q_cf, cq, st))) return r;
+    if ((r = upload(d, &d.t_cf, ct, st))) return r;
+    std::vector<int32_t> gl(d.nF), gr(d.nF);
+    auto gbase = [&](int64_t c) -> int64_t { return c < d.nQ ? 8 * c : 8 * d.nQ + 6 * (c - d.nQ); };
+    for (int64_t f = 0; f < d.nF; ++f) {
+      gl[f] = (int32_t)(gbase(m.fL[f]) + 2 * m.fkL[f]);
+      gr[f] = m.fR[f] >= 0 ? (int32_t)(gbase(m.fR[f]) + 2 * m.fkR[f]) : -1;
+    }
+    if ((r = upload(d, &d.gl, gl, st))) return r;
+    if ((r = upload(d, &d.gr, gr, st))) return r;
+    if ((r = upload_real(d, &d.fnx, m.fnx, st))) return r;
+    if ((r = upload_real(d, &d.fny, m.fny, st))) return r;
+    if ((r = upload_real(d, &d.flen, m.flen, st))) return r;
+    if ((r = upload(d, &d.fnx64, m.fnx, st))) return r;
+    if ((r = upload(d, &d.fny64, m.fny, st))) return r;
+    if ((r = upload(d, &d.flen64, m.flen, st))) return r;
+    // instance ranges (quads, triangles) and per-cell instance ids
+    std::vector<int64_t> ranges((size_t)4 * d.n_inst, 0);
+    for (int i = 0; i < d.n_inst; ++i) { ranges[4 * i] = ranges[4 * i + 1] = -1; ranges[4 * i + 2] = ranges[4 * i + 3] = -1; }
+    for (int64_t c = 0; c < d.N; ++c) {
+      const int i = m.inst[c];
+      const int part = c < d.nQ ? 0 : 2;
+      if (ranges[4 * i + part] < 0) ranges[4 * i + part] = c;
+      ranges[4 * i + part + 1] = c + 1;
+    }
+    for (auto& x : ranges) if (x < 0) x = 0;
+    if ((r = upload(d, &d.ranges, ranges, st))) return r;
+    if (d.n_inst > 1) {
+      if ((r = upload(d, &d.inst, m.inst, st))) return r;
+    }
+    CK(cudaStreamSynchronize(st));
+  }
+  // scratch
+  const int64_t ngauss = 8 * d.nQ + 6 * d.nT;
+  if ((r = d.alloc(&d.Wg, (size_t)ngauss * d.nv * d.esz))) return r;
+  if ((r = d.alloc(&d.F, (size_t)d.nF * d.nv * d.esz))) return r;
+  if ((r = d.alloc(&d.Ws, (size_t)d.N * d.nv * d.esz))) return r;
+  if (!d.fp64 && (r = d.alloc(&d.Wslo, (size_t)d.N * d.nv * d.esz))) return r;
+  if ((r = d.alloc(&d.dt_dev, sizeof(double) * d.n_inst))) return r;
+  if ((r = d.alloc(&d.red, sizeof(double) * d.n_inst * d.nv))) return r;
+  if ((r = d.alloc(&d.cell_dt, sizeof(double) * d.N))) return r;
+  if ((r = d.alloc(&d.flag, sizeof(int)))) return r;
+  CK(cudaMemsetAsync(d.flag, 0, sizeof(int), st));
+  CK(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
+  CK(cudaStreamSynchronize(st));
+  *out = s.release();
+  return WENO_OK;
+}
+
+int weno_solver_get_info(weno_solver_t s, weno_mesh_info* info) {
+  if (!s || !info) return fail(WENO_EINVAL, "null argument");
+  info->n_cells = s->N;
+  info->n_quads = s->nQ;
+  info->n_tris = s->nT;
+  info->n_faces = s->nF;
+  info->n_boundary = s->n_boundary;
+  info->n_instances = s->n_inst;
+  info->reserved = 0;
+  return WENO_OK;
+}
+
+int weno_residual(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream) {
+  if (!s || !U || !R || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  WENO_DISPATCH(*s, launch_reconstruct, *s, U, U_lo, st);
+  WENO_DISPATCH(*s, launch_face, *s, st);
+  WENO_DISPATCH(*s, launch_gather, *s, 0, const_cast<void*>(U), const_cast<void*>(U_lo), R, st);
+  return check_launch();
+}
+
+int weno_pass(weno_solver_t s, int32_t pass, const void* U, const void* U_lo, void* cuda_stream) {
+  if (!s || (pass == 1 && (!U || (!s->fp64 && !U_lo)))) return fail(WENO_EINVAL, "null argument");
+  if (pass < 1 || pass > 3) return fail(WENO_EINVAL, "pass must be 1, 2 or 3");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (pass == 1) WENO_DISPATCH(*s, launch_reconstruct, *s, U, U_lo, st);
+  else if (pass == 2) WENO_DISPATCH(*s, launch_face, *s, st);
+  else WENO_DISPATCH(*s, launch_gather, *s, 0, nullptr, nullptr, s->Ws, st);
+  return check_launch();
+}
+
+int weno_step_instances(weno_solver_t s, void* U, void* U_lo, const double* dt_dev, void* cuda_stream) {
+  if (!s || !U || !dt_dev || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (dt_dev != s->dt_dev)
+    CK(cudaMemcpyAsync(s->dt_dev, dt_dev, sizeof(double) * s->n_inst, cudaMemcpyDeviceToDevice, st));
+  cudaGraphExec_t exec = nullptr;
+  for (auto& x : s->graphs)
+    if (x.U == U && x.Ulo == U_lo) exec = x.exec;
+  if (!exec) {
+    int r = capture_step(*s, U, U_lo);
+    if (r) return r;
+    exec = s->graphs.back().exec;
+  }
+  CK(cudaGraphLaunch(exec, st));
+  return WENO_OK;
+}
+
+int weno_step(weno_solver_t s, void* U, void* U_lo, double dt, void* cuda_stream) {
+  if (!s || !U || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
+  if (!(dt >= 0)) return fail(WENO_EINVAL, "dt must be >= 0");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  weno::dev::k_fill<<<(s->n_inst + 127) / 128, 128, 0, st>>>(s->dt_dev, dt, s->n_inst);
+  int r = check_launch();
+  if (r) return r;
+  return weno_step_instances(s, U, U_lo, s->dt_dev, cuda_stream);
+}
+
+int weno_max_dt(weno_solver_t s, const void* U, const void* U_lo, double cfl, double* dt_out, void* cuda_stream) {
+  if (!s || !U || !dt_out || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  WENO_DISPATCH(*s, launch_cell_dt, *s, U, U_lo, st);
+  WENO_DISPATCH(*s, launch_reduce, *s, U, U_lo, 0, st);
+  int r = check_launch();
+  if (r) return r;
+  std::vector<double> h(s->n_inst);
+  CK(cudaMemcpyAsync(h.data(), s->red, sizeof(double) * s->n_inst, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < s->n_inst; ++i) dt_out[i] = cfl * h[i];
+  return WENO_OK;
+}
+
+int weno_conservation(weno_solver_t s, const void* U, const void* U_lo, double* sums, void* cuda_stream) {
+  if (!s || !U || !sums || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  WENO_DISPATCH(*s, launch_reduce, *s, U, U_lo, 1, st);
+  int r = check_launch();
+  if (r) return r;
+  CK(cudaMemcpyAsync(sums, s->red, sizeof(double) * s->n_inst * s->nv, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return WENO_OK;
+}
+
+int weno_check(weno_solver_t s, void* cuda_stream) {
+  if (!s) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemsetAsync(s->flag, 0, sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  if (h) return fail(WENO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or non-finite) at a Gauss point");
+  return WENO_OK;
+}
+
+int weno_solver_launch_config(weno_solver_t s, int32_t* cfg) {
+  if (!s || !cfg) return fail(WENO_EINVAL, "null argument");
+  cfg[0] = s->k1q.block; cfg[1] = s->k1q.grid;
+  cfg[2] = s->k2.block;  cfg[3] = s->k2.grid;
+  cfg[4] = s->k3q.block; cfg[5] = s->k3q.grid;
+  return WENO_OK;
+}
+
+int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_stream) {
+  if (!s || !U || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int blocks[3] = {64, 128, 256};
+  // grid candidates: one item per thread, or 1, 2, 4 resident waves of a persistent grid
+  const int waves[4] = {0, 1, 2, 4};
+  auto tune = [&](Launch& L, auto run) -> int {
+    float best = 1e30f;
+    Launch bestL = L;
+    for (int b : blocks) {
+      for (int w : waves) {
+        Launch c;
+        c.block = b;
+        c.grid = w == 0 ? 0 : w * s->nsm * std::max(1, 2048 / b);
+        L = c;
+        run();
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, st);
+          run();
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          tmin = std::min(tmin, ms);
+        }
+        if (cudaGetLastError() != cudaSuccess) continue;  // configuration not launchable
+        if (tmin < best) { best = tmin; bestL = c; }
+      }
+    }
+    L = bestL;
+    return WENO_OK;
+  };
+  S& d = *s;
+  void* u = const_cast<void*>(U);
+  void* ul = const_cast<void*>(U_lo);
+  if (d.nQ) tune(d.k1q, [&] { WENO_DISPATCH(d, launch_reconstruct, d, U, U_lo, st, 1); });
+  if (d.nT) tune(d.k1t, [&] { WENO_DISPATCH(d, launch_reconstruct, d, U, U_lo, st, 2); });
+  tune(d.k2, [&] { WENO_DISPATCH(d, launch_face, d, st); });
+  if (d.nQ) tune(d.k3q, [&] { WENO_DISPATCH(d, launch_gather, d, 0, u, ul, d.Ws, st, 1); });
+  if (d.nT) tune(d.k3t, [&] { WENO_DISPATCH(d, launch_gather, d, 0, u, ul, d.Ws, st, 2); });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  d.drop_graphs();
+  return WENO_OK;
+}
+
+void weno_solver_destroy(weno_solver_t s) { delete s; }
+
+}  // extern "C"
+
+namespace {
+
+int capture_step(S& s, void* U, void* Ulo) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(s.cap, cudaStreamCaptureModeThreadLocal));
+  WENO_DISPATCH(s, launch_step_body, s, U, Ulo, s.cap);
+  cudaError_t le = cudaGetLastError();
+  cudaError_t ce = cudaStreamEndCapture(s.cap, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(WENO_ECUDA, std::string("kernel launch in capture: ") + cudaGetErrorString(le));
+  }
+  if (ce != cudaSuccess) return fail(WENO_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(WENO_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+  if (s.graphs.size() >= 8) {
+    cudaGraphExecDestroy(s.graphs.front().exec);
+    s.graphs.erase(s.graphs.begin());
+  }
+  s.graphs.push_back({U, Ulo, exec});
+  return WENO_OK;
+}
+
+}  // namespace

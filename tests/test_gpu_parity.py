@@ -1,0 +1,207 @@
+"""CUDA path vs the FP64 CPU oracle, through the C ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import OracleMesh, OracleSolver, Params
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only machines
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1712_08317_gb300 import _capi  # noqa: E402
+from paper_1712_08317_gb300.api import Mesh, Solver  # noqa: E402
+
+# sizes span many 256-thread blocks with a ragged tail
+CASES = {
+    "scalar-quad": dict(cfg=1, kind="quad", n=40, eqn="scalar", init=S.scalar_wave),
+    "euler-tri": dict(cfg=2, kind="tri", n=24, eqn="euler", init=S.density_wave),
+    "euler-mixed": dict(cfg=2, kind="mixed", n=30, eqn="euler", init=S.density_wave),
+    "riemann-outflow": dict(cfg=3, kind="mixed", n=30, eqn="euler", init=None),
+    "vortex-lowq": dict(cfg=5, kind=None, n=36, eqn="euler", init=S.isentropic_vortex),
+}
+
+# FP64: bound on max_cells |W_gpu - W_oracle| / max_cells |W_oracle| per variable
+TOL_FP64 = 1e-11
+
+
+def _case(name):
+    c = CASES[name]
+    if c["cfg"] == 5:
+        mi = S.stretched_vortex_mesh(c["n"], seed=7)
+    else:
+        mi = S.mesh_for_config(c["cfg"], n=c["n"], seed=7, kind=c["kind"])
+    if c["init"] is None:
+        W = S.four_quadrant_average(mi, seed=7)
+    else:
+        W = S.cell_average(mi, c["init"])
+    return mi, W, c["eqn"]
+
+
+_oracles = {}
+
+
+def _oracle(name, linear=False):
+    key = (name, linear)
+    if key not in _oracles:
+        mi, W, eqn = _case(name)
+        _oracles[key] = (mi, W, OracleSolver(OracleMesh.from_input(mi), Params(eqn=eqn, linear=linear)))
+    return _oracles[key]
+
+
+def _rel(a, b):
+    scale = np.abs(b).max(axis=1, keepdims=True)
+    scale[scale == 0] = 1.0
+    return float((np.abs(a - b) / scale).max())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_residual_matches_oracle(name):
+    mi, W, osol = _oracle(name)
+    ref = osol.residual(W)
+    sol = Solver(Mesh.from_input(mi), eqn=osol.params.eqn, precision="fp64")
+    U, _ = sol.to_device(W)
+    R = sol.to_host(sol.residual(U))
+    sol.check()
+    assert _rel(R, ref) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_ten_steps_match_oracle(name):
+    mi, W, osol = _oracle(name)
+    dt = osol.max_dt(W, 0.5)
+    ref = W
+    for _ in range(10):
+        ref = osol.rk3_step(ref, dt)
+    sol = Solver(Mesh.from_input(mi), eqn=osol.params.eqn, precision="fp64")
+    U, _ = sol.to_device(W)
+    for _ in range(10):
+        sol.step(U, None, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    assert _rel(sol.to_host(U), ref) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", ["scalar-quad", "euler-mixed"])
+def test_linear_scheme_matches_oracle(name):
+    mi, W, osol = _oracle(name, linear=True)
+    ref = osol.residual(W)
+    sol = Solver(Mesh.from_input(mi), eqn=osol.params.eqn, precision="fp64", linear=True)
+    U, _ = sol.to_device(W)
+    assert _rel(sol.to_host(sol.residual(U)), ref) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", ["euler-mixed", "vortex-lowq", "riemann-outflow"])
+def test_fp32c_tracks_the_oracle(name):
+    """FP32 reconstruction / weights / flux with a compensated state: FP32-level agreement."""
+    mi, W, osol = _oracle(name)
+    ref_R = osol.residual(W)
+    dt = osol.max_dt(W, 0.5)
+    ref = W
+    for _ in range(10):
+        ref = osol.rk3_step(ref, dt)
+    sol = Solver(Mesh.from_input(mi), eqn=osol.params.eqn, precision="fp32c")
+    U, Ul = sol.to_device(W)
+    R = sol.to_host(sol.residual(U, Ul))
+    # the residual is a difference of O(1) fluxes divided by |Omega|: FP32 rounding of the
+    # fluxes, amplified by the cancellation, bounds it
+    assert _rel(R, ref_R) < 2e-3
+    for _ in range(10):
+        sol.step(U, Ul, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    assert _rel(sol.to_host(U, Ul), ref) < 2e-6
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32c", 1e-12)])
+def test_conservation_on_periodic_mesh(precision, tol):
+    mi, W, osol = _oracle("vortex-lowq")
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision=precision)
+    U, Ul = sol.to_device(W)
+    c0 = sol.conservation(U, Ul)[0]
+    dt = sol.max_dt(U, Ul, 0.5)[0]
+    for _ in range(20):
+        sol.step(U, Ul, dt)
+    c1 = sol.conservation(U, Ul)[0]
+    assert np.abs(c1 - c0).max() <= tol * np.abs(c0).max()
+    # the FP64 sums agree with the oracle's definition sum |Omega| W
+    assert np.allclose(c0, osol.conservation(W), rtol=1e-12)
+
+
+def test_max_dt_matches_oracle():
+    for name in ("euler-mixed", "scalar-quad", "riemann-outflow"):
+        mi, W, osol = _oracle(name)
+        sol = Solver(Mesh.from_input(mi), eqn=osol.params.eqn, precision="fp64")
+        U, _ = sol.to_device(W)
+        assert sol.max_dt(U, None, 0.5)[0] == pytest.approx(osol.max_dt(W, 0.5), rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_batched_instances_equal_standalone_runs(precision):
+    """One flattened launch over uneven instances with per-instance dt == separate solvers."""
+    insts = [S.mesh_for_config(2, n=13, seed=1, kind="mixed"), S.mesh_for_config(3, n=17, seed=2, kind="tri"),
+             S.mesh_for_config(2, n=9, seed=3, kind="quad")]
+    inits = [S.cell_average(insts[0], S.density_wave), S.four_quadrant_average(insts[1], 2),
+             S.cell_average(insts[2], S.density_wave)]
+    meshes = [Mesh.from_input(m) for m in insts]
+    singles = [Solver(m, eqn="euler", precision=precision) for m in meshes]
+    states = [s.to_device(w) for s, w in zip(singles, inits)]
+    dts = [s.max_dt(U, Ul, 0.4)[0] for s, (U, Ul) in zip(singles, states)]
+    for s, (U, Ul), dt in zip(singles, states, dts):
+        for _ in range(4):
+            s.step(U, Ul, dt)
+    big = Solver(Mesh.concat(meshes), eqn="euler", precision=precision)
+    Wcat = np.concatenate(inits, axis=1)
+    U, Ul = big.to_device(Wcat)
+    dt_dev = torch.tensor(dts, dtype=torch.float64, device="cuda")
+    for _ in range(4):
+        big.step_instances(U, Ul, dt_dev)
+    torch.cuda.synchronize()
+    out = big.to_host(U, Ul)
+    off = 0
+    for s, (Ui, Uli), m in zip(singles, states, insts):
+        ref = s.to_host(Ui, Uli)
+        assert np.array_equal(out[:, off:off + m.n_cells], ref)
+        off += m.n_cells
+
+
+def test_nonphysical_state_is_reported_and_cleared():
+    mi, W, _ = _oracle("euler-mixed")
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp64")
+    Wbad = W.copy()
+    Wbad[0, 5] = -0.1
+    U, _ = sol.to_device(Wbad)
+    sol.residual(U)
+    with pytest.raises(_capi.WenoError) as e:
+        sol.check()
+    assert e.value.code == _capi.WENO_ENONPHYS
+    U, _ = sol.to_device(W)
+    sol.residual(U)
+    sol.check()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_autotune_does_not_change_results(precision):
+    mi, W, _ = _oracle("euler-mixed")
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision=precision)
+    U, Ul = sol.to_device(W)
+    R0 = sol.residual(U, Ul).clone()
+    sol.autotune(U, Ul)
+    R1 = sol.residual(U, Ul)
+    assert torch.equal(R0, R1)
+    cfg = sol.launch_config()
+    assert cfg[0] in (64, 128, 256)
+
+
+def test_invalid_arguments_return_codes():
+    mi, W, _ = _oracle("euler-mixed")
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c")
+    U, Ul = sol.to_device(W)
+    lib = _capi.load()
+    import ctypes
+    # FP32C needs the compensation array
+    assert lib.weno_step(sol._h, ctypes.c_void_p(U.data_ptr()), None, 0.1, None) == _capi.WENO_EINVAL
+    assert lib.weno_step(sol._h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(Ul.data_ptr()), -1.0, None) == \
+        _capi.WENO_EINVAL

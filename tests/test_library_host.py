@@ -1,0 +1,129 @@
+"""The C-ABI library on the host: loads, exports include/weno3.h, host mesh logic vs the oracle.
+
+No compute call touches a GPU here: mesh building and the FP64 precompute
+diagnostics run on the host inside the library.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import OracleMesh, Params, precompute
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1712_08317_gb300 import _capi
+    return _capi.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    header = open(os.path.join(ROOT, "include", "weno3.h")).read()
+    declared = set(re.findall(r"^(?:int|void|const char\*)\s+(weno_[a-z0-9_]+)\s*\(", header, re.M))
+    assert len(declared) >= 18
+    so = ctypes.CDLL(lib._name)
+    for name in sorted(declared):
+        assert hasattr(so, name), name
+    from paper_1712_08317_gb300 import _capi
+    assert declared == set(_capi.SIGNATURES), declared ^ set(_capi.SIGNATURES)
+
+
+@pytest.mark.parametrize("cfg,kind,n", [(1, "quad", 9), (2, "tri", 8), (2, "mixed", 10), (3, "mixed", 10), (3, "tri", 7)])
+def test_mesh_counts_and_permutation(cfg, kind, n):
+    from paper_1712_08317_gb300.api import Mesh
+    mi = S.mesh_for_config(cfg, n=n, seed=2, kind=kind)
+    m = Mesh.from_input(mi)
+    om = OracleMesh.from_input(mi)
+    assert m.info.n_cells == mi.n_cells
+    assert m.info.n_faces == om.n_faces
+    assert m.info.n_boundary == int((om.face_R < 0).sum())
+    assert sorted(m.perm.tolist()) == list(range(mi.n_cells))
+    # internal order: quads first
+    sizes = mi.cell_sizes()[m.perm]
+    assert np.all(sizes[:m.info.n_quads] == 4) and np.all(sizes[m.info.n_quads:] == 3)
+
+
+@pytest.mark.parametrize("cfg,kind", [(1, "quad"), (2, "tri"), (2, "mixed"), (3, "mixed")])
+def test_host_precompute_matches_oracle_weights(cfg, kind):
+    """The library's own FP64 precompute (Jacobi SVD, Green moments) vs the oracle's (pinv, midpoint rule)."""
+    from paper_1712_08317_gb300.api import Mesh
+    mi = S.mesh_for_config(cfg, n=9, seed=4, kind=kind)
+    m = Mesh.from_input(mi)
+    raw, opt = m.weight_stats()
+    groups = precompute(OracleMesh.from_input(mi), Params())
+    oraw = np.zeros(mi.n_cells)
+    oopt = np.zeros(mi.n_cells)
+    for t in groups:
+        oraw[t.cells] = np.abs(t.gamma_raw).max(axis=(1, 2))
+        oopt[t.cells] = np.abs(t.gamma).max(axis=(1, 2))
+    assert np.allclose(raw, oraw[m.perm], rtol=1e-10, atol=1e-12)
+    assert np.allclose(opt, oopt[m.perm], rtol=1e-10, atol=1e-12)
+
+
+def test_batched_mesh_offsets():
+    from paper_1712_08317_gb300.api import Mesh
+    a = S.mesh_for_config(2, n=6, seed=1, kind="mixed")
+    b = S.mesh_for_config(3, n=5, seed=2, kind="tri")
+    ma, mb = Mesh.from_input(a), Mesh.from_input(b)
+    m = Mesh.concat([ma, mb])
+    assert m.info.n_instances == 2
+    assert m.n_cells == a.n_cells + b.n_cells
+    assert m.info.n_faces == ma.info.n_faces + mb.info.n_faces
+    assert sorted(m.perm.tolist()) == list(range(m.n_cells))
+    inst_of_input = np.empty(m.n_cells, int)
+    inst_of_input[m.perm] = m.instance
+    assert np.all(inst_of_input[:a.n_cells] == 0) and np.all(inst_of_input[a.n_cells:] == 1)
+    raw, opt = m.weight_stats()
+    ra, oa = ma.weight_stats()
+    # same per-cell statistics as the standalone instance
+    gid = np.empty(a.n_cells, int)
+    gid[:] = -1
+    for internal, inp in enumerate(m.perm):
+        if inp < a.n_cells:
+            gid[inp] = internal
+    assert np.array_equal(opt[gid[ma.perm]], oa)
+
+
+def _quad_mesh(nodes, cells, bc="outflow"):
+    return dict(nodes=np.array(nodes, float), cell_ptr=np.arange(0, 4 * len(cells) + 1, 4),
+                cell_nodes=np.array(cells).ravel(), bc=bc)
+
+
+def test_invalid_meshes_are_rejected_with_codes():
+    from paper_1712_08317_gb300 import _capi
+    from paper_1712_08317_gb300.api import Mesh
+    sq = [[0, 0], [1, 0], [1, 1], [0, 1], [0.4, 0.6]]
+    with pytest.raises(_capi.WenoError) as e:   # non-convex quad (reflex at node 4)
+        Mesh(**_quad_mesh(sq, [[0, 1, 4, 3]]))
+    assert e.value.code == _capi.WENO_EMESH
+    with pytest.raises(_capi.WenoError) as e:   # pentagon
+        Mesh(np.array(sq, float), [0, 5], [0, 1, 2, 3, 4], "outflow")
+    assert e.value.code == _capi.WENO_EMESH
+    with pytest.raises(_capi.WenoError) as e:   # zero area
+        Mesh(np.array([[0, 0], [1, 0], [2, 0]], float), [0, 3], [0, 1, 2], "outflow")
+    assert e.value.code == _capi.WENO_EMESH
+    mi = S.mesh_for_config(1, n=5)
+    with pytest.raises(_capi.WenoError) as e:   # wrong period: boundaries do not pair
+        Mesh(mi.nodes, mi.cell_ptr, mi.cell_nodes, "periodic", (0.0, 0.0), (2.5, 2.0))
+    assert e.value.code == _capi.WENO_EPERIODIC
+    with pytest.raises(_capi.WenoError) as e:
+        Mesh(mi.nodes, mi.cell_ptr, np.where(mi.cell_nodes == 0, 10 ** 9, mi.cell_nodes), "periodic", (0, 0), (2, 2))
+    assert e.value.code == _capi.WENO_EINVAL
+
+
+def test_clockwise_cells_are_reoriented():
+    from paper_1712_08317_gb300.api import Mesh
+    mi = S.mesh_for_config(3, n=6, seed=3, kind="mixed")
+    cn = mi.cell_nodes.copy()
+    for c in range(0, mi.n_cells, 2):
+        a, b = mi.cell_ptr[c], mi.cell_ptr[c + 1]
+        cn[a:b] = cn[a:b][::-1]
+    m1 = Mesh.from_input(mi)
+    m2 = Mesh(mi.nodes, mi.cell_ptr, cn, mi.bc, mi.origin, mi.extent)
+    assert np.array_equal(m1.perm, m2.perm)
+    assert np.array_equal(m1.weight_stats()[1], m2.weight_stats()[1])
