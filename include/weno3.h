@@ -130,6 +130,21 @@ int weno_mesh_cell_instance(weno_mesh_t mesh, int32_t* instance);
  * Runs the FP64 precompute on the host; synchronous. */
 int weno_mesh_weight_stats(weno_mesh_t mesh, const weno_params* params, double* max_raw, double* max_opt);
 
+/* Run-time tables of one cell (internal id) from the host FP64 precompute
+ * (Sections 3.1-3.3), for inspection and tests:
+ *   mg[2]            = {M, G}: 12, 8 for a quad; 9, 6 for a triangle
+ *   slot_cells[M]    internal id of the cell read for stencil slots 1..M
+ *                    (replacements resolved; a ghost reads the cell itself)
+ *   grad_op[M][4]    candidate j's gradient g_j = [o0 o1; o2 o3] (dW_a, dW_b)
+ *                    for its sub-stencil {i0, a, b}
+ *   gauss_offset[G][2] x_G - c0 of the cell's Gauss points (2 per edge,
+ *                    edge k holds points 2k (near node k) and 2k+1)
+ *   gamma[G][M]      linear weights used at run time (optimised if requested)
+ * Arrays are sized for a quad (12, 48, 16, 96 entries).  The precompute is
+ * cached on the mesh.  Synchronous, host only. */
+int weno_mesh_cell_tables(weno_mesh_t mesh, const weno_params* params, int64_t cell, int32_t* slot_cells,
+                          double* grad_op, double* gauss_offset, double* gamma, int32_t* mg);
+
 void weno_mesh_destroy(weno_mesh_t mesh);
 
 /* Creates a solver on the current CUDA device: runs the FP64 precompute

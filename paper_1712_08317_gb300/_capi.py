@@ -41,6 +41,7 @@ SIGNATURES = {
     "weno_mesh_cell_permutation": (C.c_int, [P, P]),
     "weno_mesh_cell_instance": (C.c_int, [P, P]),
     "weno_mesh_weight_stats": (C.c_int, [P, C.POINTER(weno_params), P, P]),
+    "weno_mesh_cell_tables": (C.c_int, [P, C.POINTER(weno_params), C.c_int64, P, P, P, P, P]),
     "weno_mesh_destroy": (None, [P]),
     "weno_solver_create": (C.c_int, [P, C.POINTER(weno_params), P, C.POINTER(P)]),
     "weno_solver_get_info": (C.c_int, [P, C.POINTER(weno_mesh_info)]),

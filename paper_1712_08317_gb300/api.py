@@ -71,6 +71,20 @@ class Mesh:
         capi.check(self._lib.weno_mesh_weight_stats(self._h, C.byref(p), _ptr(raw), _ptr(opt)))
         return raw, opt
 
+    def cell_tables(self, cell: int, **params):
+        """Host FP64 run-time tables of one internal cell: dict(slot, grad_op, dg, gamma)."""
+        p = params_struct(**params)
+        slot = np.zeros(12, np.int32)
+        gop = np.zeros((12, 4))
+        dg = np.zeros((8, 2))
+        gam = np.zeros(96)
+        mg = np.zeros(2, np.int32)
+        capi.check(self._lib.weno_mesh_cell_tables(self._h, C.byref(p), int(cell), _ptr(slot), _ptr(gop), _ptr(dg),
+                                                   _ptr(gam), _ptr(mg)))
+        M, G = int(mg[0]), int(mg[1])
+        return {"M": M, "G": G, "slot": slot[:M].copy(), "grad_op": gop[:M].copy(), "dg": dg[:G].copy(),
+                "gamma": gam[:G * M].reshape(G, M).copy()}
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and getattr(self, "_lib", None) is not None:

@@ -41,6 +41,28 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Double-float numbers (hi + lo, |lo| <= ulp(hi)/2): ~48-bit arithmetic from FP32
+// error-free transformations (Dekker / Knuth; products via fused multiply-add).
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df df_norm(float s, float e) {  // fast two-sum, |s| >= |e|
+  const float h = __fadd_rn(s, e);
+  return df{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_norm(s, e);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_norm(p, e);
+}
+
 // ---------------------------------------------------------------- K1
 // Threads t in [0, N*NV): cell q = t / NV of the group, variable v = t % NV.
 template <typename T, int NV, int M, int G, bool COMP>
@@ -259,11 +281,16 @@ __global__ void __launch_bounds__(256) k_face(
 //   W(s) = W^n + c_s ((W(s-1) - W^n) + dt L(W(s-1))), c = 1, 1/4, 2/3, W(0) = W^n,
 // i.e. the stages of Section 4 with the combination regrouped around W^n.
 // Stages 1, 2 write the stage buffer Ws; stage 3 writes U (= W^{n+1}).
+// COMP (FP32 fluxes, compensated state): the face sum is accumulated error-free
+// (compensated two-sum), and 1/|Omega|, dt, the RK coefficient and the state
+// update use double-float arithmetic, so that sum_i |Omega_i| dW_i telescopes
+// to ~1e-14 of the fluxes and the hi + lo state keeps its ~48-bit precision.
 template <typename T, int NV, int NFACE, bool COMP, int MODE>
 __global__ void __launch_bounds__(256) k_gather(
-    const T* __restrict__ F, const int32_t* __restrict__ cf, const T* __restrict__ inv_area, int64_t N,
-    int64_t first, T* __restrict__ U, T* __restrict__ Ulo, T* __restrict__ Ws, T* __restrict__ Wslo,
-    T* __restrict__ R, const double* __restrict__ dt, const int32_t* __restrict__ inst) {
+    const T* __restrict__ F, const int32_t* __restrict__ cf, const T* __restrict__ inv_area,
+    const T* __restrict__ inv_area_lo, int64_t N, int64_t first, T* __restrict__ U, T* __restrict__ Ulo,
+    T* __restrict__ Ws, T* __restrict__ Wslo, T* __restrict__ R, const double* __restrict__ dt,
+    const int32_t* __restrict__ inst) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = first + q;
     T acc[NV], comp[NV];
@@ -278,51 +305,56 @@ __global__ void __launch_bounds__(256) k_gather(
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const T x = e >= 0 ? -fv[v] : fv[v];  // outward flux leaves the L cell
-        if (COMP) {  // Kahan-compensated accumulation
-          const T y = x - comp[v];
-          const T s = acc[v] + y;
-          comp[v] = (s - acc[v]) - y;
+        if (COMP) {
+          float s, err;
+          two_sum((float)acc[v], (float)x, s, err);
           acc[v] = s;
+          comp[v] = __fadd_rn((float)comp[v], err);
         } else {
           acc[v] += x;
         }
       }
     }
     const T ia = __ldg(inv_area + c);
-    T res[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) res[v] = acc[v] * ia;
     if (MODE == 0) {
+      T res[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) res[v] = COMP ? (acc[v] + comp[v]) * ia : acc[v] * ia;
       store_vec<T, NV>(R + c * NV, res);
     } else {
       const double dtd = dt[inst ? __ldg(inst + c) : 0];
-      const T h = (T)dtd;
-      const T cs = MODE == 1 ? T(1) : (MODE == 2 ? T(0.25) : T(2.0 / 3.0));
       T un[NV], ws[NV], out[NV];
       load_vec<T, NV>(U + c * NV, un);
       if (MODE > 1) load_vec<T, NV>(Ws + c * NV, ws);
       if (!COMP) {
+        const T h = (T)dtd;
+        const T cs = MODE == 1 ? T(1) : (MODE == 2 ? T(0.25) : T(2.0 / 3.0));
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T d = (MODE > 1 ? ws[v] - un[v] : T(0)) + h * res[v];
+          const T d = (MODE > 1 ? ws[v] - un[v] : T(0)) + h * (acc[v] * ia);
           out[v] = un[v] + cs * d;
         }
         store_vec<T, NV>(MODE == 3 ? U + c * NV : Ws + c * NV, out);
       } else {
+        const float dth = (float)dtd;
+        const df h{dth, (float)(dtd - (double)dth)};
+        const df iad{(float)ia, (float)__ldg(inv_area_lo + c)};
+        const df cs = MODE == 1 ? df{1.0f, 0.0f} : (MODE == 2 ? df{0.25f, 0.0f} : df{0.6666667f, -1.9868216e-08f});
         T unl[NV], wsl[NV], outl[NV];
         load_vec<T, NV>(Ulo + c * NV, unl);
         if (MODE > 1) load_vec<T, NV>(Wslo + c * NV, wsl);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          // increment from W^n, small: plain FP32 is enough for it
-          const T d = (MODE > 1 ? (ws[v] - un[v]) + (wsl[v] - unl[v]) : T(0)) + h * res[v];
-          const float inc = (float)(cs * d);
-          float s, e;
-          two_sum((float)un[v], inc, s, e);
-          const float lo = __fadd_rn((float)unl[v], e);
-          const float hi = __fadd_rn(s, lo);           // renormalise (fast two-sum)
-          out[v] = hi;
-          outl[v] = __fsub_rn(lo, __fsub_rn(hi, s));
+          const df res = df_mul(df_norm((float)acc[v], (float)comp[v]), iad);
+          df d = df_mul(h, res);
+          if (MODE > 1) {
+            float s, e;
+            two_sum((float)ws[v], -(float)un[v], s, e);
+            d = df_add(d, df_norm(s, __fadd_rn(e, __fsub_rn((float)wsl[v], (float)unl[v]))));
+          }
+          const df o = df_add(df{(float)un[v], (float)unl[v]}, df_mul(cs, d));
+          out[v] = o.hi;
+          outl[v] = o.lo;
         }
         store_vec<T, NV>(MODE == 3 ? U + c * NV : Ws + c * NV, out);
         store_vec<T, NV>(MODE == 3 ? Ulo + c * NV : Wslo + c * NV, outl);

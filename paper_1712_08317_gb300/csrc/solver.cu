@@ -73,7 +73,7 @@ struct weno_solver_s {
   // device tables
   void *q_gop = nullptr, *q_dg = nullptr, *q_gam = nullptr, *t_gop = nullptr, *t_dg = nullptr, *t_gam = nullptr;
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
-  void *area = nullptr, *inv_area = nullptr;
+  void *area = nullptr, *inv_area = nullptr, *inv_area_lo = nullptr;
   double* area64 = nullptr;
   int32_t *gl = nullptr, *gr = nullptr;
   void *fnx = nullptr, *fny = nullptr, *flen = nullptr;
@@ -149,11 +149,13 @@ template <typename T, int NV, bool COMP, int MODE>
 void launch_gather_mode(S& s, void* U, void* Ulo, void* R, cudaStream_t st, int which) {
   if (s.nQ && (which & 1))
     weno::dev::k_gather<T, NV, 4, COMP, MODE><<<grid_of(s.k3q, s.nQ), s.k3q.block, 0, st>>>(
-        (const T*)s.F, s.q_cf, (const T*)s.inv_area, s.nQ, 0, (T*)U, (T*)Ulo, (T*)s.Ws, (T*)s.Wslo, (T*)R,
+        (const T*)s.F, s.q_cf, (const T*)s.inv_area, (const T*)s.inv_area_lo, s.nQ, 0, (T*)U, (T*)Ulo, (T*)s.Ws,
+        (T*)s.Wslo, (T*)R,
         s.dt_dev, s.inst);
   if (s.nT && (which & 2))
     weno::dev::k_gather<T, NV, 3, COMP, MODE><<<grid_of(s.k3t, s.nT), s.k3t.block, 0, st>>>(
-        (const T*)s.F, s.t_cf, (const T*)s.inv_area, s.nT, s.nQ, (T*)U, (T*)Ulo, (T*)s.Ws, (T*)s.Wslo, (T*)R,
+        (const T*)s.F, s.t_cf, (const T*)s.inv_area, (const T*)s.inv_area_lo, s.nT, s.nQ, (T*)U, (T*)Ulo, (T*)s.Ws,
+        (T*)s.Wslo, (T*)R,
         s.dt_dev, s.inst);
 }
 
@@ -352,6 +354,51 @@ int weno_mesh_weight_stats(weno_mesh_t mesh, const weno_params* params, double* 
   return WENO_OK;
 }
 
+int weno_mesh_cell_tables(weno_mesh_t mesh, const weno_params* params, int64_t cell, int32_t* slot_cells,
+                          double* grad_op, double* gauss_offset, double* gamma, int32_t* mg) {
+  if (!mesh || !slot_cells || !grad_op || !gauss_offset || !gamma || !mg) return fail(WENO_EINVAL, "null argument");
+  const Mesh& m = mesh->m;
+  if (cell < 0 || cell >= m.n()) return fail(WENO_EINVAL, "cell out of range");
+  weno_params p;
+  if (params) p = *params;
+  else weno_params_default(&p);
+  const double rcond = p.rcond > 0 ? p.rcond : 1e-12;
+  if (!mesh->tables || mesh->tables_rcond != rcond || mesh->tables_optimize != (p.optimize != 0)) {
+    try {
+      mesh->tables.reset();
+      auto tab = std::make_shared<std::pair<GroupTables, GroupTables>>();
+      weno::LsqParams lp;
+      lp.rcond = rcond;
+      lp.optimize = p.optimize != 0;
+      lp.n_threads = p.n_threads;
+      std::string err;
+      int r = weno::precompute_tables(m, lp, tab->first, tab->second, err);
+      if (r) return fail(r, err);
+      mesh->tables = tab;
+      mesh->tables_rcond = rcond;
+      mesh->tables_optimize = p.optimize != 0;
+    } catch (const std::bad_alloc&) {
+      return fail(WENO_ENOMEM, "host allocation failed in the precompute");
+    }
+  }
+  const bool quad = cell < m.nQ;
+  const GroupTables& T = quad ? mesh->tables->first : mesh->tables->second;
+  const int64_t q = quad ? cell : cell - m.nQ;
+  const int64_t N = T.N;
+  mg[0] = T.M;
+  mg[1] = T.G;
+  for (int j = 0; j < T.M; ++j) {
+    slot_cells[j] = T.slot[(size_t)j * N + q];
+    for (int e = 0; e < 4; ++e) grad_op[j * 4 + e] = T.gop[(size_t)(j * 4 + e) * N + q];
+  }
+  for (int g = 0; g < T.G; ++g) {
+    gauss_offset[2 * g] = T.dg[(size_t)(g * 2) * N + q];
+    gauss_offset[2 * g + 1] = T.dg[(size_t)(g * 2 + 1) * N + q];
+    for (int j = 0; j < T.M; ++j) gamma[g * T.M + j] = T.gam[(size_t)(g * T.M + j) * N + q];
+  }
+  return WENO_OK;
+}
+
 void weno_mesh_destroy(weno_mesh_t mesh) { delete mesh; }
 
 int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_stream, weno_solver_t* out) {
@@ -419,6 +466,11 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
     for (int64_t c = 0; c < d.N; ++c) inv[c] = 1.0 / m.area[c];
     if ((r = upload_real(d, &d.area, m.area, st))) return r;
     if ((r = upload_real(d, &d.inv_area, inv, st))) return r;
+    // FP32C: the rounding remainder of 1/|Omega| (double-float reciprocal)
+    std::vector<double> inv_lo(d.N, 0.0);
+    if (!d.fp64)
+      for (int64_t c = 0; c < d.N; ++c) inv_lo[c] = inv[c] - (double)(float)inv[c];
+    if ((r = upload_real(d, &d.inv_area_lo, inv_lo, st))) return r;
     if ((r = upload(d, &d.area64, m.area, st))) return r;
     CK(cudaStreamSynchronize(st));
   }
