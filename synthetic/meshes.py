@@ -108,8 +108,9 @@ def perturbed_quads(n: int, origin=(0.0, 0.0), extent=(1.0, 1.0), delta=0.1, see
 
     h is the local minimum grid spacing in each direction.  Boundary nodes stay
     put, so opposite boundaries keep matching node positions (periodic pairing
-    is exact).  Any quad that is not strictly convex has its interior nodes
-    redrawn until all quads are convex.
+    is exact).  Any quad with a corner triangle smaller than a tenth of the
+    undisplaced cell area (a sliver, or a non-convex quad) has its interior
+    nodes redrawn until no such quad is left.
     """
     nodes, quads, X, Y = quad_grid(n, origin, extent, xmap, ymap)
     rng = _rng(seed)
@@ -122,11 +123,12 @@ def perturbed_quads(n: int, origin=(0.0, 0.0), extent=(1.0, 1.0), delta=0.1, see
     amp[~interior] = 0.0
     disp = rng.uniform(-1.0, 1.0, size=nodes.shape) * amp
     pos = nodes + disp
-    # a quad must keep a clearly positive turn at every corner
+    # every corner triangle (and so both triangles of either diagonal split) must keep
+    # at least a tenth of the undisplaced cell's area: no slivers
     dx = np.diff(X)
     dy = np.diff(Y)
     cell_area = (dx[None, :] * dy[:, None]).ravel()
-    min_cross = 1e-3 * cell_area
+    min_cross = 0.2 * cell_area
     for _ in range(200):
         ok = _quads_convex(pos, quads, min_cross)
         if ok.all():
