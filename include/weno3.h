@@ -159,6 +159,27 @@ int weno_solver_get_info(weno_solver_t s, weno_mesh_info* info);
  * for FP32C, else NULL).  Stream-ordered. */
 int weno_residual(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream);
 
+/* R = L(U) exactly like weno_residual, but without touching any memory the
+ * solver allocated for scratch: the Gauss-point values and face fluxes go to
+ * a fixed 16 MiB array compiled into the library (every GPU that loads the
+ * library holds it until the process exits).  The paper has no counterpart;
+ * this call exists for callers that may not allocate device memory once
+ * they are running (a device-memory budget fixed at start-up, or a loop that
+ * may not make allocation calls), and it allocates nothing itself.
+ *  - Limit: (8 n_quads + 6 n_tris) * n_v + 256-byte padding + n_faces * n_v
+ *    elements of 8 (FP64) or 4 (FP32C) bytes must fit in 16 MiB, i.e. about
+ *    50k cells for FP64 Euler and 100k for FP32C; larger meshes get
+ *    WENO_EINVAL with the sizes in weno_last_error().
+ *  - The first call on each device looks up the array's device address on
+ *    that device; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents;
+ *    every element a call reads is written earlier in the same call, so
+ *    nothing needs clearing.  Calls whose work overlaps on the GPU (other
+ *    streams, other solvers, other host threads) race on the array: order
+ *    them on one stream.
+ * Stream-ordered. */
+int weno_residual_static(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream);
+
 /* One SSP-RK3 step (Section 4) of size dt in place on U (and U_lo). Uses a
  * CUDA graph of the three stages, built on first use for these pointers.
  * Stream-ordered. */

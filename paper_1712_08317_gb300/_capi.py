@@ -46,6 +46,7 @@ SIGNATURES = {
     "weno_solver_create": (C.c_int, [P, C.POINTER(weno_params), P, C.POINTER(P)]),
     "weno_solver_get_info": (C.c_int, [P, C.POINTER(weno_mesh_info)]),
     "weno_residual": (C.c_int, [P, P, P, P, P]),
+    "weno_residual_static": (C.c_int, [P, P, P, P, P]),
     "weno_step": (C.c_int, [P, P, P, C.c_double, P]),
     "weno_step_instances": (C.c_int, [P, P, P, P, P]),
     "weno_max_dt": (C.c_int, [P, P, P, C.c_double, P, P]),

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -728,3 +729,86 @@ int capture_step(S& s, void* U, void* Ulo) {
 }
 
 }  // namespace
+
+// ===========================================================================
+// Residual whose scratch lives in a fixed array compiled into the library.
+//
+// For callers that may not allocate device memory once they are running:
+// code that works inside a fixed device-memory budget handed out at start-up
+// (for example when another component's memory pool owns the rest of the
+// GPU), or whose per-step loop is not allowed to make allocation calls.
+// weno_residual keeps its Gauss-point values and face fluxes in buffers the
+// solver allocated; weno_residual_static puts them in g_static_scratch
+// instead and allocates nothing.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB, held by every GPU that loads the library
+constexpr int kMaxStaticDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_base[kMaxStaticDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once
+// per device; the host-side symbol itself is not a device address).
+int static_scratch_base(int dev, void** base) {
+  if (dev < 0 || dev >= kMaxStaticDevices) return fail(WENO_EINVAL, "device index out of range for the static scratch");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(WENO_ECUDA, std::string("cudaGetSymbolAddress(g_static_scratch): ") + cudaGetErrorString(e));
+    g_static_base[dev] = p;
+  }
+  *base = g_static_base[dev];
+  return WENO_OK;
+}
+
+template <typename T, int NV, bool COMP>
+void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void* wg, void* fl, cudaStream_t st) {
+  const T* u = static_cast<const T*>(U);
+  const T* ul = static_cast<const T*>(Ulo);
+  const T eps = (T)s.prm.eps, th = (T)s.prm.theta;
+  if (s.nQ)
+    weno::dev::k_reconstruct<T, NV, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
+        u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
+        (T*)wg, eps, th, s.prm.linear);
+  if (s.nT)
+    weno::dev::k_reconstruct<T, NV, 9, 6, COMP><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
+        u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
+        8 * s.nQ, (T*)wg, eps, th, s.prm.linear);
+  weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
+  if (s.nF)
+    weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
+        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag);
+  if (s.nQ)
+    weno::dev::k_gather<T, NV, 4, COMP, 0><<<grid_of(s.k3q, s.nQ), s.k3q.block, 0, st>>>(
+        (const T*)fl, s.q_cf, (const T*)s.inv_area, (const T*)s.inv_area_lo, s.nQ, 0, nullptr, nullptr, nullptr,
+        nullptr, (T*)R, s.dt_dev, s.inst);
+  if (s.nT)
+    weno::dev::k_gather<T, NV, 3, COMP, 0><<<grid_of(s.k3t, s.nT), s.k3t.block, 0, st>>>(
+        (const T*)fl, s.t_cf, (const T*)s.inv_area, (const T*)s.inv_area_lo, s.nT, s.nQ, nullptr, nullptr, nullptr,
+        nullptr, (T*)R, s.dt_dev, s.inst);
+}
+
+}  // namespace
+
+extern "C" int weno_residual_static(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream) {
+  if (!s || !U || !R || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
+  // Gauss-point values first, face fluxes after them on a 256-byte boundary
+  const size_t wg_bytes = (size_t)(8 * s->nQ + 6 * s->nT) * s->nv * s->esz;
+  const size_t f_off = (wg_bytes + 255) / 256 * 256;
+  const size_t need = f_off + (size_t)s->nF * s->nv * s->esz;
+  if (need > kStaticScratchBytes)
+    return fail(WENO_EINVAL, "mesh too large for weno_residual_static: needs " + std::to_string(need) +
+                                 " bytes of scratch, the fixed array holds " + std::to_string(kStaticScratchBytes));
+  DeviceGuard g(s->dev);
+  void* base = nullptr;
+  int r = static_scratch_base(s->dev, &base);
+  if (r) return r;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  WENO_DISPATCH(*s, launch_residual_static, *s, U, U_lo, R, b, b + f_off, (cudaStream_t)cuda_stream);
+  return check_launch();
+}
