@@ -59,7 +59,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", ARCH, "-Xcompiler", "-fPIC",
-                         f"-I{INCLUDE}", "-Xptxas", "-v", "-c", s, "-o", o])
+                         f"-I{INCLUDE}", "-Xptxas", "-v"] + os.environ.get("WENO_NVCC_FLAGS", "").split()
+                        + ["-c", s, "-o", o])
     with ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         logs = list(ex.map(_run, jobs))
     if verbose:

@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace weno {
@@ -142,6 +143,243 @@ __global__ void __launch_bounds__(256) k_reconstruct(
       }
       out[(int64_t)g * NV] = COMP ? w0 + (l0 + incr) : w0 + incr;
     }
+  }
+}
+
+// FP32C variant of K1 (same arithmetic in FP32 with approximate reciprocals).
+// Tables: gop4[j][q] = (o0 o1 o2 o3) of D_j^+, dg2[g][q] = x_G - c0,
+// gam4[g][k][q] = gamma_{4k..4k+3}, gam1[g][q] = gamma_8 (triangles).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+#ifndef WENO_K1_MIN_BLOCKS
+#define WENO_K1_MIN_BLOCKS 3  // resident 256-thread blocks per SM the register budget is sized for
+#endif
+
+// Increment R(x_G) - W0 of one Gauss point from the candidates' gradients
+// (gx, gy), beta, beta + eps and the linear weights gm (Section 3.4, FP32).
+template <int M>
+__device__ __forceinline__ float gauss_increment(const float* gx, const float* gy, const float* b, const float* be,
+                                                 const float* gm, float dx, float dy, float theta, int linear) {
+  if (linear) {
+    float incr = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) incr = fmaf(gm[j], fmaf(gx[j], dx, gy[j] * dy), incr);
+    return incr;
+  }
+  // splitting: gt+ = (gamma + theta |gamma|)/2, gt- = gt+ - gamma, sigma+- = sum gt+-
+  float sp = 0.0f, sm = 0.0f;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float tp = 0.5f * fmaf(theta, fabsf(gm[j]), gm[j]);
+    sp += tp;
+    sm += tp - gm[j];
+  }
+  const float isp = rcp_approx(sp), ism = rcp_approx(sm);
+  float Ap = 0.0f, Bp = 0.0f, Am = 0.0f, Bm = 0.0f;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float tp = 0.5f * fmaf(theta, fabsf(gm[j]), gm[j]);
+    const float gp = tp * isp, gn = (tp - gm[j]) * ism;
+    const float p = fmaf(gx[j], dx, gy[j] * dy);  // P^1_j(x_G) - W0
+    // new indicator + eps: beta (1 + q + q^2) + eps with q = gamma+- beta
+    const float qp = gp * b[j], qn = gn * b[j];
+    const float bp = fmaf(b[j], fmaf(qp, qp, qp), be[j]);
+    const float bn = fmaf(b[j], fmaf(qn, qn, qn), be[j]);
+    const float ap = gp * rcp_approx(bp * bp), an = gn * rcp_approx(bn * bn);
+    Ap += ap;
+    Bp = fmaf(ap, p, Bp);
+    Am += an;
+    Bm = fmaf(an, p, Bm);
+  }
+  return sp * Bp * rcp_approx(Ap) - sm * Bm * rcp_approx(Am);
+}
+
+// Candidate gradients and smoothness indicators of one (cell, variable).
+template <int NV, int M>
+__device__ __forceinline__ void cell_gradients(const float* __restrict__ U, const float* __restrict__ Ulo,
+                                               const int32_t* __restrict__ slot, int64_t slot_pitch,
+                                               const float4* __restrict__ gop4, int64_t pitch, int64_t q, int64_t c,
+                                               int v, float a0, float eps, float& w0, float& l0, float* gx, float* gy,
+                                               float* b, float* be) {
+  w0 = __ldg(U + c * NV + v);
+  l0 = __ldg(Ulo + c * NV + v);
+  float dW[M + 1];
+  dW[0] = 0.0f;
+#pragma unroll
+  for (int s = 1; s <= M; ++s) {
+    const int64_t cs = __ldg(slot + (int64_t)(s - 1) * slot_pitch + q);
+    dW[s] = (__ldg(U + cs * NV + v) - w0) + (__ldg(Ulo + cs * NV + v) - l0);
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
+    const float4 m = __ldg(gop4 + (int64_t)j * pitch + q);
+    gx[j] = fmaf(m.x, da, m.y * db);
+    gy[j] = fmaf(m.z, da, m.w * db);
+    b[j] = a0 * fmaf(gx[j], gx[j], gy[j] * gy[j]);
+    be[j] = b[j] + eps;
+  }
+}
+
+template <int NV, int M, int G>
+__global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
+    const float* __restrict__ U, const float* __restrict__ Ulo, const int32_t* __restrict__ slot,
+    const float4* __restrict__ gop4, const float2* __restrict__ dg2, const float4* __restrict__ gam4,
+    const float* __restrict__ gam1, const float* __restrict__ area, int64_t N, int64_t pitch, int64_t first,
+    int64_t gbase, float* __restrict__ Wg, float eps, float theta, int linear) {
+  constexpr int M4 = M / 4;
+  const int64_t total = N * NV;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / NV;
+    const int v = (int)(t - q * NV);
+    const int64_t c = first + q;
+    float w0, l0, gx[M], gy[M], b[M], be[M];
+    cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, gx, gy, b, be);
+    float* out = Wg + (gbase + q * G) * NV + v;
+#pragma unroll 1
+    for (int g = 0; g < G; ++g) {
+      const float2 d = __ldg(dg2 + (int64_t)g * pitch + q);
+      float gm[M];
+#pragma unroll
+      for (int k = 0; k < M4; ++k) {
+        const float4 x = __ldg(gam4 + (int64_t)(g * M4 + k) * pitch + q);
+        gm[4 * k] = x.x; gm[4 * k + 1] = x.y; gm[4 * k + 2] = x.z; gm[4 * k + 3] = x.w;
+      }
+      if (M % 4) gm[M - 1] = __ldg(gam1 + (int64_t)g * pitch + q);
+      const float incr = gauss_increment<M>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
+      out[(int64_t)g * NV] = w0 + (l0 + incr);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K1 with TMA-staged tables
+// Persistent kernel, Euler FP32C: a tile is 64 consecutive cells of one type,
+// one (cell, variable) per thread.  One elected thread loads the tile's linear
+// weights and Gauss offsets into shared memory with 2D TMA copies
+// (cp.async.bulk.tensor) completing on an mbarrier, double-buffered so that
+// tile i+1 streams in while tile i computes.  Every wait is bounded: on
+// timeout the block records *err = 1, drains its copies (bounded) and exits.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int M, int G>
+struct TmaTile {
+  static constexpr int TILE = 64;  // cells per tile: 256 threads = 64 cells x 4 variables
+  static constexpr int M4 = M / 4;
+  static constexpr int GAM4 = G * M4 * TILE * 16;
+  static constexpr int GAM1 = (M % 4) ? G * TILE * 4 : 0;
+  static constexpr int DG = G * TILE * 8;
+  static constexpr int STAGE = GAM4 + GAM1 + DG;  // bytes, multiple of 128
+  static constexpr int SMEM = 2 * STAGE + 16;     // two stages + two mbarriers
+};
+
+template <int M, int G>
+__global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
+    const __grid_constant__ CUtensorMap map_gam4, const __grid_constant__ CUtensorMap map_gam1,
+    const __grid_constant__ CUtensorMap map_dg, const float* __restrict__ U, const float* __restrict__ Ulo,
+    const int32_t* __restrict__ slot, const float4* __restrict__ gop4, const float* __restrict__ area, int64_t N,
+    int64_t pitch, int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, float theta, int linear,
+    int* __restrict__ err) {
+  using L = TmaTile<M, G>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (N + L::TILE - 1) / L::TILE;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tile, int stage) {
+    unsigned char* base = smem + stage * L::STAGE;
+    mbar_expect_tx(&bar[stage], L::STAGE);
+    tma_load_2d(base, &map_gam4, (int)(tile * L::TILE * 4), 0, &bar[stage]);
+    if (M % 4) tma_load_2d(base + L::GAM4, &map_gam1, (int)(tile * L::TILE), 0, &bar[stage]);
+    tma_load_2d(base + L::GAM4 + L::GAM1, &map_dg, (int)(tile * L::TILE * 2), 0, &bar[stage]);
+  };
+  int64_t tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile, 0);
+  uint32_t phase[2] = {0u, 0u};
+  for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+    const int st = i & 1;
+    const int64_t next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of that buffer
+      issue(next, st ^ 1);
+    }
+    const int64_t q = tile * L::TILE + (tid >> 2);
+    const int v = tid & 3;
+    // the stencil gathers do not depend on the staged tables: start them before waiting
+    float w0 = 0.f, l0 = 0.f, gx[M], gy[M], b[M], be[M];
+    if (q < N) {
+      const int64_t c = first + q;
+      cell_gradients<4, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, gx, gy, b, be);
+    }
+    const bool ok = mbar_wait_bounded(&bar[st], phase[st]);
+    phase[st] ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        *err = 1;
+        // drain the copy still headed for the other buffer before leaving
+        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], phase[st ^ 1]);
+      }
+      return;
+    }
+    if (q < N) {
+      const unsigned char* base = smem + st * L::STAGE;
+      const float4* sg4 = reinterpret_cast<const float4*>(base);
+      const float* sg1 = reinterpret_cast<const float*>(base + L::GAM4);
+      const float2* sdg = reinterpret_cast<const float2*>(base + L::GAM4 + L::GAM1);
+      const int cl = tid >> 2;
+      float* out = Wg + (gbase + q * G) * 4 + v;
+#pragma unroll 1
+      for (int g = 0; g < G; ++g) {
+        const float2 d = sdg[g * L::TILE + cl];
+        float gm[M];
+#pragma unroll
+        for (int k = 0; k < L::M4; ++k) {
+          const float4 x = sg4[(g * L::M4 + k) * L::TILE + cl];
+          gm[4 * k] = x.x; gm[4 * k + 1] = x.y; gm[4 * k + 2] = x.z; gm[4 * k + 3] = x.w;
+        }
+        if (M % 4) gm[M - 1] = sg1[g * L::TILE + cl];
+        const float incr = gauss_increment<M>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
+        out[(int64_t)g * 4] = w0 + (l0 + incr);
+      }
+    }
+    __syncthreads();  // the buffer is free for the copy issued in the next iteration
   }
 }
 

@@ -53,6 +53,13 @@ unsigned grid_of(const Launch& l, int64_t work) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 0x7fffffff));
 }
 
+// Persistent TMA reconstruction: 256 threads per block, one 64-cell tile per iteration.
+unsigned tma_grid(const Launch& l, int64_t cells) {
+  const int64_t tiles = (cells + 63) / 64;
+  const int64_t g = l.grid > 0 ? std::min<int64_t>(l.grid, tiles) : tiles;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 0x7fffffff));
+}
+
 }  // namespace
 
 struct weno_mesh_s {
@@ -72,7 +79,13 @@ struct weno_solver_s {
   int64_t nQ = 0, nT = 0, N = 0, nF = 0, n_boundary = 0;
   int n_inst = 1;
   // device tables
+  // FP64: SoA tables [entry][cell]; FP32C: packed (float4 / float2 per entry, cell fastest)
   void *q_gop = nullptr, *q_dg = nullptr, *q_gam = nullptr, *t_gop = nullptr, *t_dg = nullptr, *t_gam = nullptr;
+  float *q_gam1 = nullptr, *t_gam1 = nullptr;
+  int64_t q_pitch = 0, t_pitch = 0;  // row pitch (cells) of the packed FP32C tables
+  bool tma = false;                   // Euler FP32C: reconstruction with TMA-staged tables
+  CUtensorMap q_map_gam4{}, q_map_dg{}, t_map_gam4{}, t_map_gam1{}, t_map_dg{};
+  int* err = nullptr;                 // set by a kernel whose bounded wait timed out
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
   void *area = nullptr, *inv_area = nullptr, *inv_area_lo = nullptr;
   double* area64 = nullptr;
@@ -122,20 +135,52 @@ namespace {
 using S = weno_solver_s;
 
 // ------------------------------------------------------------ launches
-// which: bit 0 = quad group, bit 1 = triangle group
+// Cell reconstruction into the Gauss-value array wg.  which: bit 0 = quad group,
+// bit 1 = triangle group.
 template <typename T, int NV, bool COMP>
-void launch_reconstruct(S& s, const void* U, const void* Ulo, cudaStream_t st, int which = 3) {
+void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which) {
   const T* u = static_cast<const T*>(U);
   const T* ul = static_cast<const T*>(Ulo);
   const T eps = (T)s.prm.eps, th = (T)s.prm.theta;
-  if (s.nQ && (which & 1))
-    weno::dev::k_reconstruct<T, NV, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
-        u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
-        (T*)s.Wg, eps, th, s.prm.linear);
-  if (s.nT && (which & 2))
-    weno::dev::k_reconstruct<T, NV, 9, 6, COMP><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
-        u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
-        8 * s.nQ, (T*)s.Wg, eps, th, s.prm.linear);
+  if constexpr (COMP && NV == 4) {
+    if (s.tma) {
+      using TQ = weno::dev::TmaTile<12, 8>;
+      using TT = weno::dev::TmaTile<9, 6>;
+      if (s.nQ && (which & 1))
+        weno::dev::k_reconstruct_tma<12, 8><<<tma_grid(s.k1q, s.nQ), 256, TQ::SMEM, st>>>(
+            s.q_map_gam4, s.q_map_dg, s.q_map_dg, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
+            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, th, s.prm.linear, s.err);
+      if (s.nT && (which & 2))
+        weno::dev::k_reconstruct_tma<9, 6><<<tma_grid(s.k1t, s.nT), 256, TT::SMEM, st>>>(
+            s.t_map_gam4, s.t_map_gam1, s.t_map_dg, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
+            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, th, s.prm.linear, s.err);
+      return;
+    }
+  }
+  if constexpr (COMP) {
+    if (s.nQ && (which & 1))
+      weno::dev::k_reconstruct_f32c<NV, 12, 8><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
+          u, ul, s.q_slot, (const float4*)s.q_gop, (const float2*)s.q_dg, (const float4*)s.q_gam, s.q_gam1,
+          (const float*)s.area, s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, th, s.prm.linear);
+    if (s.nT && (which & 2))
+      weno::dev::k_reconstruct_f32c<NV, 9, 6><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
+          u, ul, s.t_slot, (const float4*)s.t_gop, (const float2*)s.t_dg, (const float4*)s.t_gam, s.t_gam1,
+          (const float*)s.area, s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, th, s.prm.linear);
+  } else {
+    if (s.nQ && (which & 1))
+      weno::dev::k_reconstruct<T, NV, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
+          u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
+          (T*)wg, eps, th, s.prm.linear);
+    if (s.nT && (which & 2))
+      weno::dev::k_reconstruct<T, NV, 9, 6, COMP><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
+          u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
+          8 * s.nQ, (T*)wg, eps, th, s.prm.linear);
+  }
+}
+
+template <typename T, int NV, bool COMP>
+void launch_reconstruct(S& s, const void* U, const void* Ulo, cudaStream_t st, int which = 3) {
+  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, s.Wg, st, which);
 }
 
 template <typename T, int NV, bool COMP>
@@ -242,6 +287,88 @@ int upload_real(S& s, void** dst, const std::vector<double>& src, cudaStream_t s
   if (r) return r;
   CK(cudaStreamSynchronize(st));  // f goes out of scope
   *dst = d;
+  return WENO_OK;
+}
+
+// FP32C tables: gop as float4 [j][q], offsets as float2 [g][q], weights as float4
+// groups [g][k][q] plus the 9th triangle weight in a float array [g][q].
+int upload_packed(S& s, const GroupTables& T, int64_t P, void** gop, void** dg, void** gam, float** gam1,
+                  cudaStream_t st) {
+  const int64_t N = T.N;
+  const int M = T.M, G = T.G, M4 = M / 4;
+  // rows of P >= N cells (padding zero) so that every row starts on a 256-byte boundary
+  std::vector<float> a((size_t)M * 4 * P, 0.f), b((size_t)G * 2 * P, 0.f), c((size_t)G * M4 * 4 * P, 0.f), e;
+  for (int j = 0; j < M; ++j)
+    for (int64_t q = 0; q < N; ++q)
+      for (int k = 0; k < 4; ++k) a[((size_t)j * P + q) * 4 + k] = (float)T.gop[((size_t)j * 4 + k) * N + q];
+  for (int g = 0; g < G; ++g)
+    for (int64_t q = 0; q < N; ++q)
+      for (int k = 0; k < 2; ++k) b[((size_t)g * P + q) * 2 + k] = (float)T.dg[((size_t)g * 2 + k) * N + q];
+  for (int g = 0; g < G; ++g)
+    for (int k4 = 0; k4 < M4; ++k4)
+      for (int64_t q = 0; q < N; ++q)
+        for (int k = 0; k < 4; ++k)
+          c[(((size_t)g * M4 + k4) * P + q) * 4 + k] = (float)T.gam[((size_t)g * M + 4 * k4 + k) * N + q];
+  if (M % 4) {
+    e.assign((size_t)G * P, 0.f);
+    for (int g = 0; g < G; ++g)
+      for (int64_t q = 0; q < N; ++q) e[(size_t)g * P + q] = (float)T.gam[((size_t)g * M + M - 1) * N + q];
+  }
+  float *pa, *pb, *pc, *pe = nullptr;
+  int r;
+  if ((r = upload(s, &pa, a, st))) return r;
+  if ((r = upload(s, &pb, b, st))) return r;
+  if ((r = upload(s, &pc, c, st))) return r;
+  if (M % 4 && (r = upload(s, &pe, e, st))) return r;
+  CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  *gop = pa;
+  *dg = pb;
+  *gam = pc;
+  *gam1 = pe;
+  return WENO_OK;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 2D float tensor map: `inner` floats per row, `rows` rows `pitch_bytes` apart, box of
+// box_inner x box_rows; out-of-range elements of the last tile are filled with zeros.
+int make_map_2d(EncodeTiled enc, CUtensorMap* map, void* base, uint64_t inner, uint64_t rows, uint64_t pitch_bytes,
+                uint32_t box_inner, uint32_t box_rows) {
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(WENO_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return WENO_OK;
+}
+
+// Tensor maps of the TMA reconstruction (Euler FP32C) and its shared-memory opt-in.
+int setup_tma(S& s) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return fail(WENO_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  EncodeTiled enc = reinterpret_cast<EncodeTiled>(fn);
+  using TQ = weno::dev::TmaTile<12, 8>;
+  using TT = weno::dev::TmaTile<9, 6>;
+  int r;
+  if (s.nQ) {
+    if ((r = make_map_2d(enc, &s.q_map_gam4, s.q_gam, 4 * s.q_pitch, 8 * 3, 16 * s.q_pitch, 256, 8 * 3))) return r;
+    if ((r = make_map_2d(enc, &s.q_map_dg, s.q_dg, 2 * s.q_pitch, 8, 8 * s.q_pitch, 128, 8))) return r;
+  }
+  if (s.nT) {
+    if ((r = make_map_2d(enc, &s.t_map_gam4, s.t_gam, 4 * s.t_pitch, 6 * 2, 16 * s.t_pitch, 256, 6 * 2))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_gam1, s.t_gam1, s.t_pitch, 6, 4 * s.t_pitch, 64, 6))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_dg, s.t_dg, 2 * s.t_pitch, 6, 8 * s.t_pitch, 128, 6))) return r;
+  }
+  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TQ::SMEM));
+  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM));
+  s.tma = true;
   return WENO_OK;
 }
 
@@ -456,12 +583,19 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   int r;
   if ((r = upload(d, &d.q_slot, tq.slot, st))) return r;
   if ((r = upload(d, &d.t_slot, tt.slot, st))) return r;
-  if ((r = upload_real(d, &d.q_gop, tq.gop, st))) return r;
-  if ((r = upload_real(d, &d.q_dg, tq.dg, st))) return r;
-  if ((r = upload_real(d, &d.q_gam, tq.gam, st))) return r;
-  if ((r = upload_real(d, &d.t_gop, tt.gop, st))) return r;
-  if ((r = upload_real(d, &d.t_dg, tt.dg, st))) return r;
-  if ((r = upload_real(d, &d.t_gam, tt.gam, st))) return r;
+  if (d.fp64) {
+    if ((r = upload_real(d, &d.q_gop, tq.gop, st))) return r;
+    if ((r = upload_real(d, &d.q_dg, tq.dg, st))) return r;
+    if ((r = upload_real(d, &d.q_gam, tq.gam, st))) return r;
+    if ((r = upload_real(d, &d.t_gop, tt.gop, st))) return r;
+    if ((r = upload_real(d, &d.t_dg, tt.dg, st))) return r;
+    if ((r = upload_real(d, &d.t_gam, tt.gam, st))) return r;
+  } else {
+    d.q_pitch = (d.nQ + 63) / 64 * 64;
+    d.t_pitch = (d.nT + 63) / 64 * 64;
+    if ((r = upload_packed(d, tq, d.q_pitch, &d.q_gop, &d.q_dg, &d.q_gam, &d.q_gam1, st))) return r;
+    if ((r = upload_packed(d, tt, d.t_pitch, &d.t_gop, &d.t_dg, &d.t_gam, &d.t_gam1, st))) return r;
+  }
   {
     std::vector<double> inv(d.N);
     for (int64_t c = 0; c < d.N; ++c) inv[c] = 1.0 / m.area[c];
@@ -531,6 +665,9 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   if ((r = d.alloc(&d.cell_dt, sizeof(double) * d.N))) return r;
   if ((r = d.alloc(&d.flag, sizeof(int)))) return r;
   CK(cudaMemsetAsync(d.flag, 0, sizeof(int), st));
+  if ((r = d.alloc(&d.err, sizeof(int)))) return r;
+  CK(cudaMemsetAsync(d.err, 0, sizeof(int), st));
+  if (!d.fp64 && d.nv == 4 && (r = setup_tma(d))) return r;
   CK(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
   CK(cudaStreamSynchronize(st));
   *out = s.release();
@@ -630,10 +767,13 @@ int weno_check(weno_solver_t s, void* cuda_stream) {
   if (!s) return fail(WENO_EINVAL, "null argument");
   DeviceGuard g(s->dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  int h = 0;
+  int h = 0, t = 0;
   CK(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&t, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemsetAsync(s->flag, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(s->err, 0, sizeof(int), st));
   CK(cudaStreamSynchronize(st));
+  if (t) return fail(WENO_ETIMEOUT, "a bounded wait for a tensor-memory copy gave up; results of that launch are invalid");
   if (h) return fail(WENO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or non-finite) at a Gauss point");
   return WENO_OK;
 }
@@ -656,14 +796,16 @@ int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_s
   const int blocks[3] = {64, 128, 256};
   // grid candidates: one item per thread, or 1, 2, 4 resident waves of a persistent grid
   const int waves[4] = {0, 1, 2, 4};
-  auto tune = [&](Launch& L, auto run) -> int {
+  std::vector<Launch> generic, tma;
+  for (int b : blocks)
+    for (int w : waves) generic.push_back(Launch{b, w == 0 ? 0 : w * s->nsm * std::max(1, 2048 / b)});
+  // TMA reconstruction: 256 threads, 1-4 resident blocks per SM, or one block per tile
+  for (int w : {0, 1, 2, 3, 4, 6}) tma.push_back(Launch{256, w * s->nsm});
+  auto tune = [&](Launch& L, auto run, const std::vector<Launch>& cands) -> int {
     float best = 1e30f;
     Launch bestL = L;
-    for (int b : blocks) {
-      for (int w : waves) {
-        Launch c;
-        c.block = b;
-        c.grid = w == 0 ? 0 : w * s->nsm * std::max(1, 2048 / b);
+    for (const Launch& c : cands) {
+      {
         L = c;
         run();
         float tmin = 1e30f;
@@ -686,11 +828,12 @@ int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_s
   S& d = *s;
   void* u = const_cast<void*>(U);
   void* ul = const_cast<void*>(U_lo);
-  if (d.nQ) tune(d.k1q, [&] { WENO_DISPATCH(d, launch_reconstruct, d, U, U_lo, st, 1); });
-  if (d.nT) tune(d.k1t, [&] { WENO_DISPATCH(d, launch_reconstruct, d, U, U_lo, st, 2); });
-  tune(d.k2, [&] { WENO_DISPATCH(d, launch_face, d, st); });
-  if (d.nQ) tune(d.k3q, [&] { WENO_DISPATCH(d, launch_gather, d, 0, u, ul, d.Ws, st, 1); });
-  if (d.nT) tune(d.k3t, [&] { WENO_DISPATCH(d, launch_gather, d, 0, u, ul, d.Ws, st, 2); });
+  const std::vector<Launch>& k1c = d.tma ? tma : generic;
+  if (d.nQ) tune(d.k1q, [&] { WENO_DISPATCH(d, launch_reconstruct, d, U, U_lo, st, 1); }, k1c);
+  if (d.nT) tune(d.k1t, [&] { WENO_DISPATCH(d, launch_reconstruct, d, U, U_lo, st, 2); }, k1c);
+  tune(d.k2, [&] { WENO_DISPATCH(d, launch_face, d, st); }, generic);
+  if (d.nQ) tune(d.k3q, [&] { WENO_DISPATCH(d, launch_gather, d, 0, u, ul, d.Ws, st, 1); }, generic);
+  if (d.nT) tune(d.k3t, [&] { WENO_DISPATCH(d, launch_gather, d, 0, u, ul, d.Ws, st, 2); }, generic);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaStreamSynchronize(st));
@@ -768,17 +911,7 @@ int static_scratch_base(int dev, void** base) {
 
 template <typename T, int NV, bool COMP>
 void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void* wg, void* fl, cudaStream_t st) {
-  const T* u = static_cast<const T*>(U);
-  const T* ul = static_cast<const T*>(Ulo);
-  const T eps = (T)s.prm.eps, th = (T)s.prm.theta;
-  if (s.nQ)
-    weno::dev::k_reconstruct<T, NV, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
-        u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
-        (T*)wg, eps, th, s.prm.linear);
-  if (s.nT)
-    weno::dev::k_reconstruct<T, NV, 9, 6, COMP><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
-        u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
-        8 * s.nQ, (T*)wg, eps, th, s.prm.linear);
+  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, wg, st, 3);
   weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
   if (s.nF)
     weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
