@@ -156,55 +156,68 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 #ifndef WENO_K1_MIN_BLOCKS
-#define WENO_K1_MIN_BLOCKS 3  // resident 256-thread blocks per SM the register budget is sized for
+#define WENO_K1_MIN_BLOCKS 2  // resident 256-thread blocks per SM the register budget is sized for
 #endif
 
-// Increment R(x_G) - W0 of one Gauss point from the candidates' gradients
-// (gx, gy), beta, beta + eps and the linear weights gm (Section 3.4, FP32).
-template <int M>
-__device__ __forceinline__ float gauss_increment(const float* gx, const float* gy, const float* b, const float* be,
-                                                 const float* gm, float dx, float dy, float theta, int linear) {
+// Paired FP32 arithmetic (Blackwell f32x2): candidates j = 2k, 2k+1 share one
+// instruction.  Odd M is padded with a candidate of weight 0 (it adds nothing).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 rcp2(float2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
+__device__ __forceinline__ float2 abs2(float2 x) { return make_float2(fabsf(x.x), fabsf(x.y)); }
+
+// Increment R(x_G) - W0 of one Gauss point (Section 3.4, FP32) from the
+// candidates' gradient pairs (gx, gy), beta, beta + eps and the linear weight
+// pairs gm.  With tp = 2 gt+ = gamma + theta|gamma| and tn = 2 gt- = tp - 2 gamma,
+// gamma+- = tp / sum tp, tn / sum tn and sigma+- = (sum tp)/2, (sum tn)/2.
+template <int P>
+__device__ __forceinline__ float gauss_increment(const float2* gx, const float2* gy, const float2* b, const float2* be,
+                                                 const float2* gm, float dx, float dy, float theta, int linear) {
+  const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy);
   if (linear) {
-    float incr = 0.0f;
+    float2 acc = f2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < M; ++j) incr = fmaf(gm[j], fmaf(gx[j], dx, gy[j] * dy), incr);
-    return incr;
+    for (int k = 0; k < P; ++k) acc = __ffma2_rn(gm[k], __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2)), acc);
+    return acc.x + acc.y;
   }
-  // splitting: gt+ = (gamma + theta |gamma|)/2, gt- = gt+ - gamma, sigma+- = sum gt+-
-  float sp = 0.0f, sm = 0.0f;
+  const float2 th2 = f2(theta, theta), m2 = f2(-2.f, -2.f);
+  float2 sp = f2(0.f, 0.f), sm = f2(0.f, 0.f);
 #pragma unroll
-  for (int j = 0; j < M; ++j) {
-    const float tp = 0.5f * fmaf(theta, fabsf(gm[j]), gm[j]);
-    sp += tp;
-    sm += tp - gm[j];
+  for (int k = 0; k < P; ++k) {
+    const float2 tp = __ffma2_rn(th2, abs2(gm[k]), gm[k]);
+    sp = __fadd2_rn(sp, tp);
+    sm = __fadd2_rn(sm, __ffma2_rn(m2, gm[k], tp));
   }
-  const float isp = rcp_approx(sp), ism = rcp_approx(sm);
-  float Ap = 0.0f, Bp = 0.0f, Am = 0.0f, Bm = 0.0f;
+  const float spt = sp.x + sp.y, smt = sm.x + sm.y;
+  const float isp = rcp_approx(spt), ism = rcp_approx(smt);
+  const float2 isp2 = f2(isp, isp), ism2 = f2(ism, ism);
+  float2 Ap = f2(0.f, 0.f), Bp = f2(0.f, 0.f), Am = f2(0.f, 0.f), Bm = f2(0.f, 0.f);
 #pragma unroll
-  for (int j = 0; j < M; ++j) {
-    const float tp = 0.5f * fmaf(theta, fabsf(gm[j]), gm[j]);
-    const float gp = tp * isp, gn = (tp - gm[j]) * ism;
-    const float p = fmaf(gx[j], dx, gy[j] * dy);  // P^1_j(x_G) - W0
+  for (int k = 0; k < P; ++k) {
+    const float2 tp = __ffma2_rn(th2, abs2(gm[k]), gm[k]);
+    const float2 gp = __fmul2_rn(tp, isp2), gn = __fmul2_rn(__ffma2_rn(m2, gm[k], tp), ism2);
+    const float2 p = __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2));  // P^1_j(x_G) - W0
     // new indicator + eps: beta (1 + q + q^2) + eps with q = gamma+- beta
-    const float qp = gp * b[j], qn = gn * b[j];
-    const float bp = fmaf(b[j], fmaf(qp, qp, qp), be[j]);
-    const float bn = fmaf(b[j], fmaf(qn, qn, qn), be[j]);
-    const float ap = gp * rcp_approx(bp * bp), an = gn * rcp_approx(bn * bn);
-    Ap += ap;
-    Bp = fmaf(ap, p, Bp);
-    Am += an;
-    Bm = fmaf(an, p, Bm);
+    const float2 qp = __fmul2_rn(gp, b[k]), qn = __fmul2_rn(gn, b[k]);
+    const float2 bp = __ffma2_rn(b[k], __ffma2_rn(qp, qp, qp), be[k]);
+    const float2 bn = __ffma2_rn(b[k], __ffma2_rn(qn, qn, qn), be[k]);
+    const float2 ap = __fmul2_rn(gp, rcp2(__fmul2_rn(bp, bp)));
+    const float2 an = __fmul2_rn(gn, rcp2(__fmul2_rn(bn, bn)));
+    Ap = __fadd2_rn(Ap, ap);
+    Bp = __ffma2_rn(ap, p, Bp);
+    Am = __fadd2_rn(Am, an);
+    Bm = __ffma2_rn(an, p, Bm);
   }
-  return sp * Bp * rcp_approx(Ap) - sm * Bm * rcp_approx(Am);
+  return 0.5f * spt * (Bp.x + Bp.y) * rcp_approx(Ap.x + Ap.y) - 0.5f * smt * (Bm.x + Bm.y) * rcp_approx(Am.x + Am.y);
 }
 
-// Candidate gradients and smoothness indicators of one (cell, variable).
+// Candidate gradients and smoothness indicators of one (cell, variable), as
+// candidate pairs (the padding candidate of odd M has g = 0, beta = 0).
 template <int NV, int M>
 __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, const float* __restrict__ Ulo,
                                                const int32_t* __restrict__ slot, int64_t slot_pitch,
                                                const float4* __restrict__ gop4, int64_t pitch, int64_t q, int64_t c,
-                                               int v, float a0, float eps, float& w0, float& l0, float* gx, float* gy,
-                                               float* b, float* be) {
+                                               int v, float a0, float eps, float& w0, float& l0, float2* gx2,
+                                               float2* gy2, float2* b2, float2* be2) {
   w0 = __ldg(U + c * NV + v);
   l0 = __ldg(Ulo + c * NV + v);
   float dW[M + 1];
@@ -214,6 +227,7 @@ __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, cons
     const int64_t cs = __ldg(slot + (int64_t)(s - 1) * slot_pitch + q);
     dW[s] = (__ldg(U + cs * NV + v) - w0) + (__ldg(Ulo + cs * NV + v) - l0);
   }
+  float gx[2 * ((M + 1) / 2)], gy[2 * ((M + 1) / 2)], b[2 * ((M + 1) / 2)];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const float da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
@@ -221,7 +235,14 @@ __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, cons
     gx[j] = fmaf(m.x, da, m.y * db);
     gy[j] = fmaf(m.z, da, m.w * db);
     b[j] = a0 * fmaf(gx[j], gx[j], gy[j] * gy[j]);
-    be[j] = b[j] + eps;
+  }
+  if (M % 2) { gx[M] = 0.f; gy[M] = 0.f; b[M] = 0.f; }
+#pragma unroll
+  for (int k = 0; k < (M + 1) / 2; ++k) {
+    gx2[k] = f2(gx[2 * k], gx[2 * k + 1]);
+    gy2[k] = f2(gy[2 * k], gy[2 * k + 1]);
+    b2[k] = f2(b[2 * k], b[2 * k + 1]);
+    be2[k] = f2(b[2 * k] + eps, b[2 * k + 1] + eps);
   }
 }
 
@@ -237,20 +258,23 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
     const int64_t q = t / NV;
     const int v = (int)(t - q * NV);
     const int64_t c = first + q;
-    float w0, l0, gx[M], gy[M], b[M], be[M];
+    constexpr int P = (M + 1) / 2;
+    float w0, l0;
+    float2 gx[P], gy[P], b[P], be[P];
     cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, gx, gy, b, be);
     float* out = Wg + (gbase + q * G) * NV + v;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
       const float2 d = __ldg(dg2 + (int64_t)g * pitch + q);
-      float gm[M];
+      float2 gm[P];
 #pragma unroll
       for (int k = 0; k < M4; ++k) {
         const float4 x = __ldg(gam4 + (int64_t)(g * M4 + k) * pitch + q);
-        gm[4 * k] = x.x; gm[4 * k + 1] = x.y; gm[4 * k + 2] = x.z; gm[4 * k + 3] = x.w;
+        gm[2 * k] = f2(x.x, x.y);
+        gm[2 * k + 1] = f2(x.z, x.w);
       }
-      if (M % 4) gm[M - 1] = __ldg(gam1 + (int64_t)g * pitch + q);
-      const float incr = gauss_increment<M>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
+      if (M % 4) gm[P - 1] = f2(__ldg(gam1 + (int64_t)g * pitch + q), 0.f);
+      const float incr = gauss_increment<P>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
       out[(int64_t)g * NV] = w0 + (l0 + incr);
     }
   }
@@ -343,7 +367,9 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
     const int64_t q = tile * L::TILE + (tid >> 2);
     const int v = tid & 3;
     // the stencil gathers do not depend on the staged tables: start them before waiting
-    float w0 = 0.f, l0 = 0.f, gx[M], gy[M], b[M], be[M];
+    constexpr int P = (M + 1) / 2;
+    float w0 = 0.f, l0 = 0.f;
+    float2 gx[P], gy[P], b[P], be[P];
     if (q < N) {
       const int64_t c = first + q;
       cell_gradients<4, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, gx, gy, b, be);
@@ -368,14 +394,15 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
 #pragma unroll 1
       for (int g = 0; g < G; ++g) {
         const float2 d = sdg[g * L::TILE + cl];
-        float gm[M];
+        float2 gm[P];
 #pragma unroll
         for (int k = 0; k < L::M4; ++k) {
           const float4 x = sg4[(g * L::M4 + k) * L::TILE + cl];
-          gm[4 * k] = x.x; gm[4 * k + 1] = x.y; gm[4 * k + 2] = x.z; gm[4 * k + 3] = x.w;
+          gm[2 * k] = f2(x.x, x.y);
+          gm[2 * k + 1] = f2(x.z, x.w);
         }
-        if (M % 4) gm[M - 1] = sg1[g * L::TILE + cl];
-        const float incr = gauss_increment<M>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
+        if (M % 4) gm[P - 1] = f2(sg1[g * L::TILE + cl], 0.f);
+        const float incr = gauss_increment<P>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
         out[(int64_t)g * 4] = w0 + (l0 + incr);
       }
     }

@@ -799,8 +799,8 @@ int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_s
   std::vector<Launch> generic, tma;
   for (int b : blocks)
     for (int w : waves) generic.push_back(Launch{b, w == 0 ? 0 : w * s->nsm * std::max(1, 2048 / b)});
-  // TMA reconstruction: 256 threads, 1-4 resident blocks per SM, or one block per tile
-  for (int w : {0, 1, 2, 3, 4, 6}) tma.push_back(Launch{256, w * s->nsm});
+  // TMA reconstruction: 256 threads; 1-4 blocks per SM (persistent), or one block per tile
+  for (int w : {0, 1, 2, 3, 4}) tma.push_back(Launch{256, w * s->nsm});
   auto tune = [&](Launch& L, auto run, const std::vector<Launch>& cands) -> int {
     float best = 1e30f;
     Launch bestL = L;
