@@ -166,48 +166,43 @@ __device__ __forceinline__ float2 rcp2(float2 x) { return make_float2(rcp_approx
 __device__ __forceinline__ float2 abs2(float2 x) { return make_float2(fabsf(x.x), fabsf(x.y)); }
 
 // Increment R(x_G) - W0 of one Gauss point (Section 3.4, FP32) from the
-// candidates' gradient pairs (gx, gy), beta, beta + eps and the linear weight
-// pairs gm.  With tp = 2 gt+ = gamma + theta|gamma| and tn = 2 gt- = tp - 2 gamma,
-// gamma+- = tp / sum tp, tn / sum tn and sigma+- = (sum tp)/2, (sum tn)/2.
+// candidates' gradient pairs (gx, gy), beta, beta + eps, and the split linear
+// weights gamma+ (gpos), gamma- (gneg) with their sums sigma+- (sp, sm), which
+// depend on geometry only and are precomputed in FP64:
+//   R - W0 = sigma+ sum delta+ p - sigma- sum delta- p,
+//   delta+-_j = alpha+-_j / sum alpha+-, alpha+-_j = gamma+-_j / (beta~+-_j + eps)^2,
+//   beta~+-_j = beta_j (1 + q + q^2), q = gamma+-_j beta_j.
+// The linear scheme is R - W0 = sum gamma_j p_j = sigma+ sum gamma+ p - sigma- sum gamma- p.
 template <int P>
 __device__ __forceinline__ float gauss_increment(const float2* gx, const float2* gy, const float2* b, const float2* be,
-                                                 const float2* gm, float dx, float dy, float theta, int linear) {
+                                                 const float2* gpos, const float2* gneg, float dx, float dy, float sp,
+                                                 float sm, int linear) {
   const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy);
   if (linear) {
-    float2 acc = f2(0.f, 0.f);
+    float2 ap = f2(0.f, 0.f), an = f2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < P; ++k) acc = __ffma2_rn(gm[k], __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2)), acc);
-    return acc.x + acc.y;
+    for (int k = 0; k < P; ++k) {
+      const float2 p = __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2));
+      ap = __ffma2_rn(gpos[k], p, ap);
+      an = __ffma2_rn(gneg[k], p, an);
+    }
+    return sp * (ap.x + ap.y) - sm * (an.x + an.y);
   }
-  const float2 th2 = f2(theta, theta), m2 = f2(-2.f, -2.f);
-  float2 sp = f2(0.f, 0.f), sm = f2(0.f, 0.f);
-#pragma unroll
-  for (int k = 0; k < P; ++k) {
-    const float2 tp = __ffma2_rn(th2, abs2(gm[k]), gm[k]);
-    sp = __fadd2_rn(sp, tp);
-    sm = __fadd2_rn(sm, __ffma2_rn(m2, gm[k], tp));
-  }
-  const float spt = sp.x + sp.y, smt = sm.x + sm.y;
-  const float isp = rcp_approx(spt), ism = rcp_approx(smt);
-  const float2 isp2 = f2(isp, isp), ism2 = f2(ism, ism);
   float2 Ap = f2(0.f, 0.f), Bp = f2(0.f, 0.f), Am = f2(0.f, 0.f), Bm = f2(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    const float2 tp = __ffma2_rn(th2, abs2(gm[k]), gm[k]);
-    const float2 gp = __fmul2_rn(tp, isp2), gn = __fmul2_rn(__ffma2_rn(m2, gm[k], tp), ism2);
     const float2 p = __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2));  // P^1_j(x_G) - W0
-    // new indicator + eps: beta (1 + q + q^2) + eps with q = gamma+- beta
-    const float2 qp = __fmul2_rn(gp, b[k]), qn = __fmul2_rn(gn, b[k]);
+    const float2 qp = __fmul2_rn(gpos[k], b[k]), qn = __fmul2_rn(gneg[k], b[k]);
     const float2 bp = __ffma2_rn(b[k], __ffma2_rn(qp, qp, qp), be[k]);
     const float2 bn = __ffma2_rn(b[k], __ffma2_rn(qn, qn, qn), be[k]);
-    const float2 ap = __fmul2_rn(gp, rcp2(__fmul2_rn(bp, bp)));
-    const float2 an = __fmul2_rn(gn, rcp2(__fmul2_rn(bn, bn)));
+    const float2 ap = __fmul2_rn(gpos[k], rcp2(__fmul2_rn(bp, bp)));
+    const float2 an = __fmul2_rn(gneg[k], rcp2(__fmul2_rn(bn, bn)));
     Ap = __fadd2_rn(Ap, ap);
     Bp = __ffma2_rn(ap, p, Bp);
     Am = __fadd2_rn(Am, an);
     Bm = __ffma2_rn(an, p, Bm);
   }
-  return 0.5f * spt * (Bp.x + Bp.y) * rcp_approx(Ap.x + Ap.y) - 0.5f * smt * (Bm.x + Bm.y) * rcp_approx(Am.x + Am.y);
+  return sp * (Bp.x + Bp.y) * rcp_approx(Ap.x + Ap.y) - sm * (Bm.x + Bm.y) * rcp_approx(Am.x + Am.y);
 }
 
 // Candidate gradients and smoothness indicators of one (cell, variable), as
@@ -246,35 +241,42 @@ __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, cons
   }
 }
 
+// FP32C tables (rows of `pitch` cells): gop4[j] = D_j^+ entries; dgs[g] =
+// (x_G - c0, sigma+, sigma-); gpm4[g][k] = gamma+_{4k..4k+3} for k < M/4 and
+// gamma-_{4(k-M/4)..} after them; g1[g] = (gamma+_8, gamma-_8) for triangles.
 template <int NV, int M, int G>
 __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
     const float* __restrict__ U, const float* __restrict__ Ulo, const int32_t* __restrict__ slot,
-    const float4* __restrict__ gop4, const float2* __restrict__ dg2, const float4* __restrict__ gam4,
-    const float* __restrict__ gam1, const float* __restrict__ area, int64_t N, int64_t pitch, int64_t first,
-    int64_t gbase, float* __restrict__ Wg, float eps, float theta, int linear) {
-  constexpr int M4 = M / 4;
+    const float4* __restrict__ gop4, const float4* __restrict__ dgs, const float4* __restrict__ gpm4,
+    const float2* __restrict__ g1, const float* __restrict__ area, int64_t N, int64_t pitch, int64_t first,
+    int64_t gbase, float* __restrict__ Wg, float eps, int linear) {
+  constexpr int M4 = M / 4, P = (M + 1) / 2;
   const int64_t total = N * NV;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = t / NV;
     const int v = (int)(t - q * NV);
     const int64_t c = first + q;
-    constexpr int P = (M + 1) / 2;
     float w0, l0;
     float2 gx[P], gy[P], b[P], be[P];
     cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, gx, gy, b, be);
     float* out = Wg + (gbase + q * G) * NV + v;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
-      const float2 d = __ldg(dg2 + (int64_t)g * pitch + q);
-      float2 gm[P];
+      const float4 d = __ldg(dgs + (int64_t)g * pitch + q);
+      float2 gp[P], gn[P];
 #pragma unroll
       for (int k = 0; k < M4; ++k) {
-        const float4 x = __ldg(gam4 + (int64_t)(g * M4 + k) * pitch + q);
-        gm[2 * k] = f2(x.x, x.y);
-        gm[2 * k + 1] = f2(x.z, x.w);
+        const float4 x = __ldg(gpm4 + (int64_t)(g * 2 * M4 + k) * pitch + q);
+        const float4 y = __ldg(gpm4 + (int64_t)(g * 2 * M4 + M4 + k) * pitch + q);
+        gp[2 * k] = f2(x.x, x.y); gp[2 * k + 1] = f2(x.z, x.w);
+        gn[2 * k] = f2(y.x, y.y); gn[2 * k + 1] = f2(y.z, y.w);
       }
-      if (M % 4) gm[P - 1] = f2(__ldg(gam1 + (int64_t)g * pitch + q), 0.f);
-      const float incr = gauss_increment<P>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
+      if (M % 4) {
+        const float2 e = __ldg(g1 + (int64_t)g * pitch + q);
+        gp[P - 1] = f2(e.x, 0.f);
+        gn[P - 1] = f2(e.y, 0.f);
+      }
+      const float incr = gauss_increment<P>(gx, gy, b, be, gp, gn, d.x, d.y, d.z, d.w, linear);
       out[(int64_t)g * NV] = w0 + (l0 + incr);
     }
   }
@@ -321,21 +323,22 @@ template <int M, int G>
 struct TmaTile {
   static constexpr int TILE = 64;  // cells per tile: 256 threads = 64 cells x 4 variables
   static constexpr int M4 = M / 4;
-  static constexpr int GAM4 = G * M4 * TILE * 16;
-  static constexpr int GAM1 = (M % 4) ? G * TILE * 4 : 0;
-  static constexpr int DG = G * TILE * 8;
-  static constexpr int STAGE = GAM4 + GAM1 + DG;  // bytes, multiple of 128
-  static constexpr int SMEM = 2 * STAGE + 16;     // two stages + two mbarriers
+  static constexpr int GPM = G * 2 * M4 * TILE * 16;          // gamma+ rows then gamma- rows
+  static constexpr int DGS = G * TILE * 16;                    // (x_G - c0, sigma+, sigma-)
+  static constexpr int G1 = (M % 4) ? G * TILE * 8 : 0;        // (gamma+_8, gamma-_8) of triangles
+  static constexpr int STAGE = GPM + DGS + G1;                 // bytes, multiple of 128
+  static constexpr int SMEM = 2 * STAGE + 16;                  // two stages + two mbarriers
 };
 
 template <int M, int G>
 __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
-    const __grid_constant__ CUtensorMap map_gam4, const __grid_constant__ CUtensorMap map_gam1,
-    const __grid_constant__ CUtensorMap map_dg, const float* __restrict__ U, const float* __restrict__ Ulo,
+    const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
+    const __grid_constant__ CUtensorMap map_g1, const float* __restrict__ U, const float* __restrict__ Ulo,
     const int32_t* __restrict__ slot, const float4* __restrict__ gop4, const float* __restrict__ area, int64_t N,
-    int64_t pitch, int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, float theta, int linear,
+    int64_t pitch, int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, int linear,
     int* __restrict__ err) {
   using L = TmaTile<M, G>;
+  constexpr int P = (M + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
   const int tid = threadIdx.x;
@@ -350,9 +353,9 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
   auto issue = [&](int64_t tile, int stage) {
     unsigned char* base = smem + stage * L::STAGE;
     mbar_expect_tx(&bar[stage], L::STAGE);
-    tma_load_2d(base, &map_gam4, (int)(tile * L::TILE * 4), 0, &bar[stage]);
-    if (M % 4) tma_load_2d(base + L::GAM4, &map_gam1, (int)(tile * L::TILE), 0, &bar[stage]);
-    tma_load_2d(base + L::GAM4 + L::GAM1, &map_dg, (int)(tile * L::TILE * 2), 0, &bar[stage]);
+    tma_load_2d(base, &map_gpm, (int)(tile * L::TILE * 4), 0, &bar[stage]);
+    tma_load_2d(base + L::GPM, &map_dgs, (int)(tile * L::TILE * 4), 0, &bar[stage]);
+    if (M % 4) tma_load_2d(base + L::GPM + L::DGS, &map_g1, (int)(tile * L::TILE * 2), 0, &bar[stage]);
   };
   int64_t tile = blockIdx.x;
   if (tid == 0 && tile < ntiles) issue(tile, 0);
@@ -367,7 +370,6 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
     const int64_t q = tile * L::TILE + (tid >> 2);
     const int v = tid & 3;
     // the stencil gathers do not depend on the staged tables: start them before waiting
-    constexpr int P = (M + 1) / 2;
     float w0 = 0.f, l0 = 0.f;
     float2 gx[P], gy[P], b[P], be[P];
     if (q < N) {
@@ -386,23 +388,28 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
     }
     if (q < N) {
       const unsigned char* base = smem + st * L::STAGE;
-      const float4* sg4 = reinterpret_cast<const float4*>(base);
-      const float* sg1 = reinterpret_cast<const float*>(base + L::GAM4);
-      const float2* sdg = reinterpret_cast<const float2*>(base + L::GAM4 + L::GAM1);
+      const float4* sgp = reinterpret_cast<const float4*>(base);
+      const float4* sds = reinterpret_cast<const float4*>(base + L::GPM);
+      const float2* sg1 = reinterpret_cast<const float2*>(base + L::GPM + L::DGS);
       const int cl = tid >> 2;
       float* out = Wg + (gbase + q * G) * 4 + v;
 #pragma unroll 1
       for (int g = 0; g < G; ++g) {
-        const float2 d = sdg[g * L::TILE + cl];
-        float2 gm[P];
+        const float4 d = sds[g * L::TILE + cl];
+        float2 gp[P], gn[P];
 #pragma unroll
         for (int k = 0; k < L::M4; ++k) {
-          const float4 x = sg4[(g * L::M4 + k) * L::TILE + cl];
-          gm[2 * k] = f2(x.x, x.y);
-          gm[2 * k + 1] = f2(x.z, x.w);
+          const float4 x = sgp[(g * 2 * L::M4 + k) * L::TILE + cl];
+          const float4 y = sgp[(g * 2 * L::M4 + L::M4 + k) * L::TILE + cl];
+          gp[2 * k] = f2(x.x, x.y); gp[2 * k + 1] = f2(x.z, x.w);
+          gn[2 * k] = f2(y.x, y.y); gn[2 * k + 1] = f2(y.z, y.w);
         }
-        if (M % 4) gm[P - 1] = f2(sg1[g * L::TILE + cl], 0.f);
-        const float incr = gauss_increment<P>(gx, gy, b, be, gm, d.x, d.y, theta, linear);
+        if (M % 4) {
+          const float2 e = sg1[g * L::TILE + cl];
+          gp[P - 1] = f2(e.x, 0.f);
+          gn[P - 1] = f2(e.y, 0.f);
+        }
+        const float incr = gauss_increment<P>(gx, gy, b, be, gp, gn, d.x, d.y, d.z, d.w, linear);
         out[(int64_t)g * 4] = w0 + (l0 + incr);
       }
     }

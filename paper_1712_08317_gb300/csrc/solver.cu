@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -79,12 +80,14 @@ struct weno_solver_s {
   int64_t nQ = 0, nT = 0, N = 0, nF = 0, n_boundary = 0;
   int n_inst = 1;
   // device tables
-  // FP64: SoA tables [entry][cell]; FP32C: packed (float4 / float2 per entry, cell fastest)
+  // FP64: SoA tables [entry][cell] (gop, dg, gam).  FP32C: packed rows of float4 / float2
+  // with the cell fastest: gop = D_j^+ entries, dg = (x_G - c0, sigma+, sigma-),
+  // gam = gamma+ then gamma- rows, gam1 = (gamma+_8, gamma-_8) of triangles.
   void *q_gop = nullptr, *q_dg = nullptr, *q_gam = nullptr, *t_gop = nullptr, *t_dg = nullptr, *t_gam = nullptr;
-  float *q_gam1 = nullptr, *t_gam1 = nullptr;
+  void *q_gam1 = nullptr, *t_gam1 = nullptr;
   int64_t q_pitch = 0, t_pitch = 0;  // row pitch (cells) of the packed FP32C tables
   bool tma = false;                   // Euler FP32C: reconstruction with TMA-staged tables
-  CUtensorMap q_map_gam4{}, q_map_dg{}, t_map_gam4{}, t_map_gam1{}, t_map_dg{};
+  CUtensorMap q_map_gpm{}, q_map_dgs{}, t_map_gpm{}, t_map_dgs{}, t_map_g1{};
   int* err = nullptr;                 // set by a kernel whose bounded wait timed out
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
   void *area = nullptr, *inv_area = nullptr, *inv_area_lo = nullptr;
@@ -148,24 +151,25 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
       using TT = weno::dev::TmaTile<9, 6>;
       if (s.nQ && (which & 1))
         weno::dev::k_reconstruct_tma<12, 8><<<tma_grid(s.k1q, s.nQ), 256, TQ::SMEM, st>>>(
-            s.q_map_gam4, s.q_map_dg, s.q_map_dg, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
-            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, th, s.prm.linear, s.err);
+            s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
+            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err);
       if (s.nT && (which & 2))
         weno::dev::k_reconstruct_tma<9, 6><<<tma_grid(s.k1t, s.nT), 256, TT::SMEM, st>>>(
-            s.t_map_gam4, s.t_map_gam1, s.t_map_dg, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
-            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, th, s.prm.linear, s.err);
+            s.t_map_gpm, s.t_map_dgs, s.t_map_g1, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
+            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err);
       return;
     }
   }
   if constexpr (COMP) {
     if (s.nQ && (which & 1))
       weno::dev::k_reconstruct_f32c<NV, 12, 8><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
-          u, ul, s.q_slot, (const float4*)s.q_gop, (const float2*)s.q_dg, (const float4*)s.q_gam, s.q_gam1,
-          (const float*)s.area, s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, th, s.prm.linear);
+          u, ul, s.q_slot, (const float4*)s.q_gop, (const float4*)s.q_dg, (const float4*)s.q_gam,
+          (const float2*)s.q_gam1, (const float*)s.area, s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear);
     if (s.nT && (which & 2))
       weno::dev::k_reconstruct_f32c<NV, 9, 6><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
-          u, ul, s.t_slot, (const float4*)s.t_gop, (const float2*)s.t_dg, (const float4*)s.t_gam, s.t_gam1,
-          (const float*)s.area, s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, th, s.prm.linear);
+          u, ul, s.t_slot, (const float4*)s.t_gop, (const float4*)s.t_dg, (const float4*)s.t_gam,
+          (const float2*)s.t_gam1, (const float*)s.area, s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps,
+          s.prm.linear);
   } else {
     if (s.nQ && (which & 1))
       weno::dev::k_reconstruct<T, NV, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
@@ -290,29 +294,48 @@ int upload_real(S& s, void** dst, const std::vector<double>& src, cudaStream_t s
   return WENO_OK;
 }
 
-// FP32C tables: gop as float4 [j][q], offsets as float2 [g][q], weights as float4
-// groups [g][k][q] plus the 9th triangle weight in a float array [g][q].
-int upload_packed(S& s, const GroupTables& T, int64_t P, void** gop, void** dg, void** gam, float** gam1,
-                  cudaStream_t st) {
+// FP32C tables, rows of P >= N cells (padding zero, every row on a 256-byte boundary):
+//   gop [j][q]        float4 D_j^+ entries
+//   dg  [g][q]        float4 (x_G - c0, sigma+, sigma-)
+//   gam [g][k][q]     float4 rows: gamma+_{4k..4k+3} for k < M/4, then gamma- rows
+//   gam1 [g][q]       float2 (gamma+_8, gamma-_8) of triangles
+// The splitting of Section 3.4 depends on the geometry only; it is evaluated
+// here in FP64: gt+ = (gamma + theta|gamma|)/2, gt- = gt+ - gamma,
+// sigma+- = sum gt+-, gamma+- = gt+- / sigma+-.
+int upload_packed(S& s, const GroupTables& T, int64_t P, double theta, void** gop, void** dg, void** gam,
+                  void** gam1, cudaStream_t st) {
   const int64_t N = T.N;
   const int M = T.M, G = T.G, M4 = M / 4;
-  // rows of P >= N cells (padding zero) so that every row starts on a 256-byte boundary
-  std::vector<float> a((size_t)M * 4 * P, 0.f), b((size_t)G * 2 * P, 0.f), c((size_t)G * M4 * 4 * P, 0.f), e;
+  std::vector<float> a((size_t)M * 4 * P, 0.f), b((size_t)G * 4 * P, 0.f), c((size_t)G * 2 * M4 * 4 * P, 0.f), e;
+  if (M % 4) e.assign((size_t)G * 2 * P, 0.f);
   for (int j = 0; j < M; ++j)
     for (int64_t q = 0; q < N; ++q)
       for (int k = 0; k < 4; ++k) a[((size_t)j * P + q) * 4 + k] = (float)T.gop[((size_t)j * 4 + k) * N + q];
-  for (int g = 0; g < G; ++g)
-    for (int64_t q = 0; q < N; ++q)
-      for (int k = 0; k < 2; ++k) b[((size_t)g * P + q) * 2 + k] = (float)T.dg[((size_t)g * 2 + k) * N + q];
-  for (int g = 0; g < G; ++g)
-    for (int k4 = 0; k4 < M4; ++k4)
-      for (int64_t q = 0; q < N; ++q)
-        for (int k = 0; k < 4; ++k)
-          c[(((size_t)g * M4 + k4) * P + q) * 4 + k] = (float)T.gam[((size_t)g * M + 4 * k4 + k) * N + q];
-  if (M % 4) {
-    e.assign((size_t)G * P, 0.f);
-    for (int g = 0; g < G; ++g)
-      for (int64_t q = 0; q < N; ++q) e[(size_t)g * P + q] = (float)T.gam[((size_t)g * M + M - 1) * N + q];
+  std::vector<double> gp(M), gn(M);
+  for (int g = 0; g < G; ++g) {
+    for (int64_t q = 0; q < N; ++q) {
+      double sp = 0.0, sm = 0.0;
+      for (int j = 0; j < M; ++j) {
+        const double x = T.gam[((size_t)g * M + j) * N + q];
+        gp[j] = 0.5 * (x + theta * std::fabs(x));
+        gn[j] = gp[j] - x;
+        sp += gp[j];
+        sm += gn[j];
+      }
+      float* d = &b[((size_t)g * P + q) * 4];
+      d[0] = (float)T.dg[((size_t)g * 2 + 0) * N + q];
+      d[1] = (float)T.dg[((size_t)g * 2 + 1) * N + q];
+      d[2] = (float)sp;
+      d[3] = (float)sm;
+      for (int j = 0; j < 4 * M4; ++j) {
+        c[(((size_t)g * 2 * M4 + j / 4) * P + q) * 4 + j % 4] = (float)(gp[j] / sp);
+        c[(((size_t)g * 2 * M4 + M4 + j / 4) * P + q) * 4 + j % 4] = (float)(gn[j] / sm);
+      }
+      if (M % 4) {
+        e[((size_t)g * P + q) * 2] = (float)(gp[M - 1] / sp);
+        e[((size_t)g * P + q) * 2 + 1] = (float)(gn[M - 1] / sm);
+      }
+    }
   }
   float *pa, *pb, *pc, *pe = nullptr;
   int r;
@@ -357,14 +380,15 @@ int setup_tma(S& s) {
   using TQ = weno::dev::TmaTile<12, 8>;
   using TT = weno::dev::TmaTile<9, 6>;
   int r;
+  // rows: gamma+-: G * 2 * (M/4) float4 rows; (x_G - c0, sigma+-): G float4 rows; triangle extras: G float2 rows
   if (s.nQ) {
-    if ((r = make_map_2d(enc, &s.q_map_gam4, s.q_gam, 4 * s.q_pitch, 8 * 3, 16 * s.q_pitch, 256, 8 * 3))) return r;
-    if ((r = make_map_2d(enc, &s.q_map_dg, s.q_dg, 2 * s.q_pitch, 8, 8 * s.q_pitch, 128, 8))) return r;
+    if ((r = make_map_2d(enc, &s.q_map_gpm, s.q_gam, 4 * s.q_pitch, 8 * 6, 16 * s.q_pitch, 256, 8 * 6))) return r;
+    if ((r = make_map_2d(enc, &s.q_map_dgs, s.q_dg, 4 * s.q_pitch, 8, 16 * s.q_pitch, 256, 8))) return r;
   }
   if (s.nT) {
-    if ((r = make_map_2d(enc, &s.t_map_gam4, s.t_gam, 4 * s.t_pitch, 6 * 2, 16 * s.t_pitch, 256, 6 * 2))) return r;
-    if ((r = make_map_2d(enc, &s.t_map_gam1, s.t_gam1, s.t_pitch, 6, 4 * s.t_pitch, 64, 6))) return r;
-    if ((r = make_map_2d(enc, &s.t_map_dg, s.t_dg, 2 * s.t_pitch, 6, 8 * s.t_pitch, 128, 6))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_gpm, s.t_gam, 4 * s.t_pitch, 6 * 4, 16 * s.t_pitch, 256, 6 * 4))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_dgs, s.t_dg, 4 * s.t_pitch, 6, 16 * s.t_pitch, 256, 6))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_g1, s.t_gam1, 2 * s.t_pitch, 6, 8 * s.t_pitch, 128, 6))) return r;
   }
   CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TQ::SMEM));
   CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM));
@@ -593,8 +617,8 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   } else {
     d.q_pitch = (d.nQ + 63) / 64 * 64;
     d.t_pitch = (d.nT + 63) / 64 * 64;
-    if ((r = upload_packed(d, tq, d.q_pitch, &d.q_gop, &d.q_dg, &d.q_gam, &d.q_gam1, st))) return r;
-    if ((r = upload_packed(d, tt, d.t_pitch, &d.t_gop, &d.t_dg, &d.t_gam, &d.t_gam1, st))) return r;
+    if ((r = upload_packed(d, tq, d.q_pitch, p.theta, &d.q_gop, &d.q_dg, &d.q_gam, &d.q_gam1, st))) return r;
+    if ((r = upload_packed(d, tt, d.t_pitch, p.theta, &d.t_gop, &d.t_dg, &d.t_gam, &d.t_gam1, st))) return r;
   }
   {
     std::vector<double> inv(d.N);

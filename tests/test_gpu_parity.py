@@ -98,7 +98,7 @@ def test_linear_scheme_matches_oracle(name):
     assert _rel(sol.to_host(sol.residual(U)), ref) < TOL_FP64
 
 
-@pytest.mark.parametrize("name", ["euler-mixed", "vortex-lowq", "riemann-outflow"])
+@pytest.mark.parametrize("name", ["euler-mixed", "vortex-lowq", "riemann-outflow", "scalar-quad", "euler-tri"])
 def test_fp32c_tracks_the_oracle(name):
     """FP32 reconstruction / weights / flux with a compensated state: FP32-level agreement."""
     mi, W, osol = _oracle(name)
