@@ -174,10 +174,10 @@ __device__ __forceinline__ float2 abs2(float2 x) { return make_float2(fabsf(x.x)
 //   beta~+-_j = beta_j (1 + q + q^2), q = gamma+-_j beta_j.
 // The linear scheme is R - W0 = sum gamma_j p_j = sigma+ sum gamma+ p - sigma- sum gamma- p.
 template <int P>
-__device__ __forceinline__ float gauss_increment(const float2* gx, const float2* gy, const float2* b, const float2* be,
+__device__ __forceinline__ float gauss_increment(const float2* gx, const float2* gy, const float2* b, float eps,
                                                  const float2* gpos, const float2* gneg, float dx, float dy, float sp,
                                                  float sm, int linear) {
-  const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy);
+  const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy), eps2 = f2(eps, eps);
   if (linear) {
     float2 ap = f2(0.f, 0.f), an = f2(0.f, 0.f);
 #pragma unroll
@@ -193,8 +193,9 @@ __device__ __forceinline__ float gauss_increment(const float2* gx, const float2*
   for (int k = 0; k < P; ++k) {
     const float2 p = __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2));  // P^1_j(x_G) - W0
     const float2 qp = __fmul2_rn(gpos[k], b[k]), qn = __fmul2_rn(gneg[k], b[k]);
-    const float2 bp = __ffma2_rn(b[k], __ffma2_rn(qp, qp, qp), be[k]);
-    const float2 bn = __ffma2_rn(b[k], __ffma2_rn(qn, qn, qn), be[k]);
+    const float2 be = __fadd2_rn(b[k], eps2);
+    const float2 bp = __ffma2_rn(b[k], __ffma2_rn(qp, qp, qp), be);
+    const float2 bn = __ffma2_rn(b[k], __ffma2_rn(qn, qn, qn), be);
     const float2 ap = __fmul2_rn(gpos[k], rcp2(__fmul2_rn(bp, bp)));
     const float2 an = __fmul2_rn(gneg[k], rcp2(__fmul2_rn(bn, bn)));
     Ap = __fadd2_rn(Ap, ap);
@@ -211,8 +212,8 @@ template <int NV, int M>
 __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, const float* __restrict__ Ulo,
                                                const int32_t* __restrict__ slot, int64_t slot_pitch,
                                                const float4* __restrict__ gop4, int64_t pitch, int64_t q, int64_t c,
-                                               int v, float a0, float eps, float& w0, float& l0, float2* gx2,
-                                               float2* gy2, float2* b2, float2* be2) {
+                                               int v, float a0, float& w0, float& l0, float2* gx2, float2* gy2,
+                                               float2* b2) {
   w0 = __ldg(U + c * NV + v);
   l0 = __ldg(Ulo + c * NV + v);
   float dW[M + 1];
@@ -237,7 +238,6 @@ __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, cons
     gx2[k] = f2(gx[2 * k], gx[2 * k + 1]);
     gy2[k] = f2(gy[2 * k], gy[2 * k + 1]);
     b2[k] = f2(b[2 * k], b[2 * k + 1]);
-    be2[k] = f2(b[2 * k] + eps, b[2 * k + 1] + eps);
   }
 }
 
@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
     const int v = (int)(t - q * NV);
     const int64_t c = first + q;
     float w0, l0;
-    float2 gx[P], gy[P], b[P], be[P];
-    cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, gx, gy, b, be);
+    float2 gx[P], gy[P], b[P];
+    cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), w0, l0, gx, gy, b);
     float* out = Wg + (gbase + q * G) * NV + v;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
         gp[P - 1] = f2(e.x, 0.f);
         gn[P - 1] = f2(e.y, 0.f);
       }
-      const float incr = gauss_increment<P>(gx, gy, b, be, gp, gn, d.x, d.y, d.z, d.w, linear);
+      const float incr = gauss_increment<P>(gx, gy, b, eps, gp, gn, d.x, d.y, d.z, d.w, linear);
       out[(int64_t)g * NV] = w0 + (l0 + incr);
     }
   }
@@ -284,11 +284,15 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
 
 // ---------------------------------------------------------------- K1 with TMA-staged tables
 // Persistent kernel, Euler FP32C: a tile is 64 consecutive cells of one type,
-// one (cell, variable) per thread.  One elected thread loads the tile's linear
-// weights and Gauss offsets into shared memory with 2D TMA copies
-// (cp.async.bulk.tensor) completing on an mbarrier, double-buffered so that
-// tile i+1 streams in while tile i computes.  Every wait is bounded: on
-// timeout the block records *err = 1, drains its copies (bounded) and exits.
+// one (cell, variable) per thread.  One elected thread loads the tile's split
+// linear weights and Gauss offsets into shared memory with 2D TMA copies
+// (cp.async.bulk.tensor) completing on an mbarrier; the stencil gathers of the
+// tile are issued before the wait.  With one buffer (default) the next tile's
+// copy starts when the block has finished reading the current one and the
+// other resident block hides its latency, which leaves more of the unified
+// L1 to the gathers than two buffers would; WENO_K1_STAGES=2 prefetches the
+// next tile instead.  Every wait is bounded: on timeout the block records
+// *err = 1, drains its copies (bounded) and exits.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -319,6 +323,10 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+#ifndef WENO_K1_STAGES
+#define WENO_K1_STAGES 1  // shared-memory table buffers per block (2: prefetch the next tile while computing)
+#endif
+
 template <int M, int G>
 struct TmaTile {
   static constexpr int TILE = 64;  // cells per tile: 256 threads = 64 cells x 4 variables
@@ -327,7 +335,8 @@ struct TmaTile {
   static constexpr int DGS = G * TILE * 16;                    // (x_G - c0, sigma+, sigma-)
   static constexpr int G1 = (M % 4) ? G * TILE * 8 : 0;        // (gamma+_8, gamma-_8) of triangles
   static constexpr int STAGE = GPM + DGS + G1;                 // bytes, multiple of 128
-  static constexpr int SMEM = 2 * STAGE + 16;                  // two stages + two mbarriers
+  static constexpr int NSTAGE = WENO_K1_STAGES;
+  static constexpr int SMEM = NSTAGE * STAGE + 16;             // stages + two mbarriers
 };
 
 template <int M, int G>
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
   using L = TmaTile<M, G>;
   constexpr int P = (M + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::NSTAGE * L::STAGE);
   const int tid = threadIdx.x;
   const int64_t ntiles = (N + L::TILE - 1) / L::TILE;
   if (tid == 0) {
@@ -361,9 +370,9 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
   if (tid == 0 && tile < ntiles) issue(tile, 0);
   uint32_t phase[2] = {0u, 0u};
   for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
-    const int st = i & 1;
+    const int st = L::NSTAGE == 2 ? (i & 1) : 0;
     const int64_t next = tile + gridDim.x;
-    if (tid == 0 && next < ntiles) {
+    if (L::NSTAGE == 2 && tid == 0 && next < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of that buffer
       issue(next, st ^ 1);
     }
@@ -371,10 +380,10 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
     const int v = tid & 3;
     // the stencil gathers do not depend on the staged tables: start them before waiting
     float w0 = 0.f, l0 = 0.f;
-    float2 gx[P], gy[P], b[P], be[P];
+    float2 gx[P], gy[P], b[P];
     if (q < N) {
       const int64_t c = first + q;
-      cell_gradients<4, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, gx, gy, b, be);
+      cell_gradients<4, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), w0, l0, gx, gy, b);
     }
     const bool ok = mbar_wait_bounded(&bar[st], phase[st]);
     phase[st] ^= 1u;
@@ -382,7 +391,7 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
       if (tid == 0) {
         *err = 1;
         // drain the copy still headed for the other buffer before leaving
-        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], phase[st ^ 1]);
+        if (L::NSTAGE == 2 && next < ntiles) mbar_wait_bounded(&bar[st ^ 1], phase[st ^ 1]);
       }
       return;
     }
@@ -409,11 +418,15 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
           gp[P - 1] = f2(e.x, 0.f);
           gn[P - 1] = f2(e.y, 0.f);
         }
-        const float incr = gauss_increment<P>(gx, gy, b, be, gp, gn, d.x, d.y, d.z, d.w, linear);
+        const float incr = gauss_increment<P>(gx, gy, b, eps, gp, gn, d.x, d.y, d.z, d.w, linear);
         out[(int64_t)g * 4] = w0 + (l0 + incr);
       }
     }
     __syncthreads();  // the buffer is free for the copy issued in the next iteration
+    if (L::NSTAGE == 1 && tid == 0 && next < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(next, 0);
+    }
   }
 }
 
