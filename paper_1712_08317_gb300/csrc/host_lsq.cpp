@@ -10,13 +10,14 @@
 //   eta(x_G) = p(x_G)^T A^+ (Eq. 13), eta_0 = 1 - sum eta_j.
 //   candidate j on {i0, a, b}: g_j = D_j^+ (dW_a, dW_b), D_j = [c_a - c0; c_b - c0].
 //   B (slots x candidates) from P^1_j(x_G) = W0 + (x_G - c0) . g_j (Eq. 14),
-//   gamma = B^+ eta (Eq. 15).
+//   gamma = B^+ eta (Eq. 15), by a complete orthogonal decomposition of B.
 //   Section 3.3: d_j from |gamma| at the same Gauss point, eta^opt from the
 //   weighted rows d_j A_j, gamma^opt = B^+ eta^opt.
 // The zeta-regularised normal equations of Eqs. 12 and 15 are read as their
-// zeta -> 0 limit, the minimum-norm least-squares solution, computed here by
-// one-sided Jacobi SVD (Hestenes) with singular values below
-// rcond * sigma_max dropped.
+// zeta -> 0 limit, the minimum-norm least-squares solution: for the small
+// A and D_j systems by one-sided Jacobi SVD (Hestenes) with singular values
+// below rcond * sigma_max dropped; for B by QR with column pivoting (rank
+// from |R_jj| > rcond |R_00|) completed by an RZ step.
 #include "host_lsq.hpp"
 
 #include <algorithm>
@@ -84,6 +85,108 @@ void pinv_jacobi(const double* A, int m, int n, double rcond, double* P) {
       for (int j = 0; j < n; ++j) s += V[k * n + j] * inv2[j] * W[i * n + j];
       P[k * m + i] = s;
     }
+}
+
+void minnorm_cod(const double* A, int m, int n, const double* Bk, int k, double rcond, double* X) {
+  // Complete orthogonal decomposition (Golub & Van Loan, Sec. 5.4-5.5):
+  // A P = Q [R11 R12; 0 0] with column pivoting (rank r from |R_jj| > rcond |R_00|),
+  // [R11 R12] = [T 0] Z^T by Householder reflections from the right, then the
+  // minimum-norm solution x = P Z [T^{-1} (Q^T b)_{1..r}; 0].
+  double W[16 * 16], R[16 * 16];
+  int piv[16];
+  for (int i = 0; i < m * n; ++i) W[i] = A[i];
+  for (int i = 0; i < m * k; ++i) R[i] = Bk[i];  // right-hand sides, m x k
+  for (int j = 0; j < n; ++j) piv[j] = j;
+  const int t = std::min(m, n);
+  double r00 = 0.0;
+  int r = 0;
+  for (int j = 0; j < t; ++j) {
+    // pivot: largest remaining column norm
+    int best = j;
+    double bn = -1.0;
+    for (int c = j; c < n; ++c) {
+      double s = 0.0;
+      for (int i = j; i < m; ++i) s += W[i * n + c] * W[i * n + c];
+      if (s > bn) { bn = s; best = c; }
+    }
+    if (best != j) {
+      for (int i = 0; i < m; ++i) std::swap(W[i * n + j], W[i * n + best]);
+      std::swap(piv[j], piv[best]);
+    }
+    const double nrm = std::sqrt(bn);
+    if (j == 0) r00 = nrm;
+    if (!(nrm > rcond * r00) || nrm == 0.0) break;
+    r = j + 1;
+    // Householder reflector v (v_j = x_j - alpha) zeroing W[j+1.., j]
+    const double x0 = W[j * n + j];
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    double v[16];
+    for (int i = j; i < m; ++i) v[i] = W[i * n + j];
+    v[j] = x0 - alpha;
+    double vv = 0.0;
+    for (int i = j; i < m; ++i) vv += v[i] * v[i];
+    if (vv > 0.0) {
+      const double tau = 2.0 / vv;
+      for (int c = j; c < n; ++c) {
+        double d = 0.0;
+        for (int i = j; i < m; ++i) d += v[i] * W[i * n + c];
+        d *= tau;
+        for (int i = j; i < m; ++i) W[i * n + c] -= d * v[i];
+      }
+      for (int c = 0; c < k; ++c) {
+        double d = 0.0;
+        for (int i = j; i < m; ++i) d += v[i] * R[i * k + c];
+        d *= tau;
+        for (int i = j; i < m; ++i) R[i * k + c] -= d * v[i];
+      }
+    }
+    W[j * n + j] = alpha;
+    for (int i = j + 1; i < m; ++i) W[i * n + j] = 0.0;
+  }
+  // RZ: reflect columns {i, r..n-1} of rows 0..i so that row i of R12 vanishes
+  double zv[16][16];
+  double ztau[16];
+  for (int i = r - 1; i >= 0; --i) {
+    if (r == n) { ztau[i] = 0.0; continue; }
+    double a2 = W[i * n + i] * W[i * n + i];
+    for (int c = r; c < n; ++c) a2 += W[i * n + c] * W[i * n + c];
+    const double nrm = std::sqrt(a2);
+    const double x0 = W[i * n + i];
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    double* v = zv[i];
+    v[0] = x0 - alpha;  // coordinate i
+    double vv = v[0] * v[0];
+    for (int c = r; c < n; ++c) { v[1 + c - r] = W[i * n + c]; vv += v[1 + c - r] * v[1 + c - r]; }
+    ztau[i] = vv > 0.0 ? 2.0 / vv : 0.0;
+    for (int row = 0; row <= i; ++row) {
+      double d = v[0] * W[row * n + i];
+      for (int c = r; c < n; ++c) d += v[1 + c - r] * W[row * n + c];
+      d *= ztau[i];
+      W[row * n + i] -= d * v[0];
+      for (int c = r; c < n; ++c) W[row * n + c] -= d * v[1 + c - r];
+    }
+  }
+  for (int c = 0; c < k; ++c) {
+    double w[16];
+    for (int i = 0; i < n; ++i) w[i] = 0.0;
+    // T y = (Q^T b)_{0..r-1}, T upper triangular in W[0..r-1][0..r-1]
+    for (int i = r - 1; i >= 0; --i) {
+      double s = R[i * k + c];
+      for (int j = i + 1; j < r; ++j) s -= W[i * n + j] * w[j];
+      w[i] = s / W[i * n + i];
+    }
+    // x~ = Z w = H_{r-1} ... H_0 w: apply H_0 first
+    for (int i = 0; i < r; ++i) {
+      if (ztau[i] == 0.0) continue;
+      const double* v = zv[i];
+      double d = v[0] * w[i];
+      for (int cc = r; cc < n; ++cc) d += v[1 + cc - r] * w[cc];
+      d *= ztau[i];
+      w[i] -= d * v[0];
+      for (int cc = r; cc < n; ++cc) w[cc] -= d * v[1 + cc - r];
+    }
+    for (int i = 0; i < n; ++i) X[piv[i] * k + c] = w[i];
+  }
 }
 
 namespace {
@@ -180,15 +283,9 @@ void cell_tables(const Mesh& m, const LsqParams& p, int64_t c, GroupTables& T, i
       B[res[sub[j][1]] * M + j] += t1;
       B[0 * M + j] += 1.0 - t0 - t1;
     }
-    double Bp[12 * 13];
-    pinv_jacobi(B, R, M, p.rcond, Bp);
     double gam[12];
-    for (int j = 0; j < M; ++j) {
-      double s = 0.0;
-      for (int r = 0; r < R; ++r) s += Bp[j * R + r] * eta[r];
-      gam[j] = s;
-      mraw = std::max(mraw, std::fabs(s));
-    }
+    minnorm_cod(B, R, M, eta, 1, p.rcond, gam);
+    for (int j = 0; j < M; ++j) mraw = std::max(mraw, std::fabs(gam[j]));
     if (p.optimize) {
       double d[12];
       for (int j = 0; j < M; ++j) d[j] = 1.0;
@@ -199,23 +296,19 @@ void cell_tables(const Mesh& m, const LsqParams& p, int64_t c, GroupTables& T, i
         for (auto& jk : pr)
           d[jk[0] - 1] = 1.0 / std::max(std::max(1.0, std::fabs(gam[jk[0] - 1])), std::fabs(gam[jk[1] - 1]));
       }
-      double DA[12 * 5], DAp[5 * 12];
+      // eta^opt_j = d_j [p^T (DA)^+]_j, and p^T (DA)^+ is the minimum-norm solution
+      // y of (DA)^T y = p (the pseudo-inverse of a transpose is the transpose of it)
+      double DAt[5 * 12], y[12];
       for (int j = 0; j < M; ++j)
-        for (int kk = 0; kk < 5; ++kk) DA[j * 5 + kk] = d[j] * A[j * 5 + kk];
-      pinv_jacobi(DA, M, 5, p.rcond, DAp);
+        for (int kk = 0; kk < 5; ++kk) DAt[kk * M + j] = d[j] * A[j * 5 + kk];
+      minnorm_cod(DAt, 5, M, pg, 1, p.rcond, y);
       sum = 0.0;
       for (int j = 1; j < R; ++j) {
-        double s = 0.0;
-        for (int kk = 0; kk < 5; ++kk) s += pg[kk] * DAp[kk * M + (j - 1)];
-        eta[j] = s * d[j - 1];
+        eta[j] = y[j - 1] * d[j - 1];
         sum += eta[j];
       }
       eta[0] = 1.0 - sum;
-      for (int j = 0; j < M; ++j) {
-        double s = 0.0;
-        for (int r = 0; r < R; ++r) s += Bp[j * R + r] * eta[r];
-        gam[j] = s;
-      }
+      minnorm_cod(B, R, M, eta, 1, p.rcond, gam);
     }
     // weights at rounding level are zero in exact arithmetic (e.g. a candidate
     // made of i0 and its outflow ghost only, whose beta is always 0, so the

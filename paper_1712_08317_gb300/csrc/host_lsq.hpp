@@ -34,4 +34,8 @@ int precompute_tables(const Mesh& m, const LsqParams& p, GroupTables& quads, Gro
 // Moore-Penrose pseudo-inverse (exposed for the library's own self-checks).
 void pinv_jacobi(const double* A, int m, int n, double rcond, double* P);
 
+// Minimum-norm least-squares solutions X (n x k) of A X = B (A m x n, B m x k, m, n <= 16)
+// by a complete orthogonal decomposition with column pivoting.
+void minnorm_cod(const double* A, int m, int n, const double* B, int k, double rcond, double* X);
+
 }  // namespace weno
