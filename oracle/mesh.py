@@ -11,9 +11,15 @@ Conventions (fixed readings, shared in writing with the CUDA library):
   period ("node classes"); a neighbour reached through a periodic face is
   translated by the period so that it sits next to the cell (the paper is
   silent; the least-squares geometry needs it).
-* Outflow boundaries: the face neighbour across a boundary face is a ghost,
-  the mirror image of the cell across that face, whose value is the cell's
-  own average; ghosts have no children.
+* Outflow boundaries (reading): the stencil is continued by mirror images
+  across boundary faces.  The face neighbour across a boundary face is the
+  mirror image of i0 (a ghost with i0's average); a child reached through a
+  boundary face of a real face neighbour is that neighbour's mirror image;
+  the children of a ghost are the mirror images (across the ghost's face) of
+  the cells across i0's other faces at that node (a corner gives a double
+  mirror of i0).  A mirror image carries the average of the cell it mirrors
+  (zero-gradient outflow).  Without them, corner stencils become so
+  degenerate that the optimised linear weights reach |gamma| ~ 300.
 * Stencil (figures of Sections 3.1 and 3.2 are missing): the "child of face
   neighbour i_m at node v" is the cell across i_m's other face incident to v.
   Quad: i1..i4 across faces 0..3; i5, i6 = children of i1 at v0, v1;
@@ -21,9 +27,9 @@ Conventions (fixed readings, shared in writing with the CUDA library):
   i9, i12 = children of i4 at v0, v3.  Triangle: i1..i3 across faces 0..2;
   i4, i8 = children of i1 at v0, v1; i5, i9 = children of i2 at v1, v2;
   i6, i7 = children of i3 at v2, v0.
-  A child does not exist when it lies across a boundary face, when it is
-  i0 or one of the face neighbours, or (second tier: quad i9..i12, triangle
-  i7..i9) when it is the cell of its partner slot.  Missing first-tier cells
+  A child does not exist when it is i0 or one of the face neighbours, or
+  (second tier: quad i9..i12, triangle i7..i9) when it is its partner slot's
+  cell; images are compared by (cell, mirror faces).  Missing first-tier cells
   are replaced by i0, missing second-tier cells by their partner
   (quad i_{j-4}, triangle i_{j-3}), and get E_j = 0.
 """
@@ -213,8 +219,37 @@ class OracleMesh:
                 self.cell_gauss[c, 2 * k + 1] = GAUSS_B * a + GAUSS_A * b
 
     # ------------------------------------------------------------------ stencils
+    def _image_across(self, c: int, k: int):
+        """Image across local face k of (real) cell c: (kind, cell, shift, mirror faces)."""
+        x, sh = self.neighbour(c, k)
+        if x >= 0:
+            return (SLOT_CELL, x, sh, ())
+        return (SLOT_GHOST, c, np.zeros(2), (self.cell_face[c][k],))
+
+    def _child_image(self, c: int, k: int, at_start: bool, parent):
+        """Child of the face-k neighbour image `parent` of c at node k (at_start) or k+1."""
+        kind, p, sh, refl = parent
+        m = len(self.cells[c])
+        if kind == SLOT_CELL:
+            f = self.cell_face[c][k]
+            km = self.cell_face[p].index(f)
+            nm = len(self.cells[p])
+            other = (km + 1) % nm if at_start else (km - 1) % nm
+            x, sh2 = self.neighbour(p, other)
+            if x >= 0:
+                return (SLOT_CELL, x, sh + sh2, ())
+            return (SLOT_GHOST, p, sh.copy(), (self.cell_face[p][other],))
+        # parent = mirror of c across its face k: mirror the image across c's other face at that node
+        k2 = (k - 1) % m if at_start else (k + 1) % m
+        y = self._image_across(c, k2)
+        return (SLOT_GHOST, y[1], y[2], y[3] + (self.cell_face[c][k],))
+
+    @staticmethod
+    def _identity(img):
+        return (img[1], img[3])
+
     def _stencils(self):
-        """slots[c] = list of (kind, cell, shift, E, ghost_face) for i0..iM."""
+        """slots[c] = list of (kind, cell, shift, E, mirror faces) for i0..iM."""
         self.slots = []
         for c, ids in enumerate(self.cells):
             quad = len(ids) == 4
@@ -222,56 +257,62 @@ class OracleMesh:
             children = QUAD_CHILDREN if quad else TRI_CHILDREN
             replace = QUAD_REPLACE if quad else TRI_REPLACE
             s = [None] * (M + 1)
-            s[0] = (SLOT_CELL, c, np.zeros(2), 1, -1)
-            face_cells = {c}
+            s[0] = (SLOT_CELL, c, np.zeros(2), 1, ())
+            images = [(SLOT_CELL, c, np.zeros(2), ())]
             for k in range(len(ids)):
-                x, sh = self.neighbour(c, k)
-                if x < 0:
-                    s[k + 1] = (SLOT_GHOST, c, np.zeros(2), 1, k)
-                else:
-                    s[k + 1] = (SLOT_CELL, x, sh, 1, -1)
-                    face_cells.add(x)
+                img = self._image_across(c, k)
+                images.append(img)
+                s[k + 1] = (img[0], img[1], img[2], 1, img[3])
+            taken = {self._identity(i) for i in images}
             first_tier = [j for j, r in replace.items() if r == 0]
             ordered = sorted(children, key=lambda t: (t[0] not in first_tier, t[0]))
             for (j, k, at_start) in ordered:
-                parent = s[k + 1]
-                x, sh = (-1, None) if parent[0] == SLOT_GHOST else self.child(c, k, at_start)
-                missing = x < 0 or x in face_cells
+                parent = images[k + 1]
+                img = self._child_image(c, k, at_start, parent)
+                ident = self._identity(img)
+                missing = ident in taken
                 r = replace[j]
                 if not missing and r != 0:
-                    pj = s[r]
-                    partner_cell = pj[1] if pj[0] == SLOT_CELL else c
-                    missing = (x == partner_cell)
+                    pj = s[self.resolve_partial(s, r, replace)]
+                    missing = ident == (pj[1], pj[4])
                 if missing:
-                    s[j] = (SLOT_MISSING, -1, None, 0, -1)
+                    s[j] = (SLOT_MISSING, -1, None, 0, ())
                 else:
-                    s[j] = (SLOT_CELL, x, sh, 1, -1)
+                    s[j] = (img[0], img[1], img[2], 1, img[3])
             self.slots.append(s)
+
+    @staticmethod
+    def resolve_partial(s, j, replace):
+        while s[j][0] == SLOT_MISSING:
+            j = replace[j]
+        return j
 
     def resolve(self, c: int, j: int) -> int:
         """Slot whose cell a (possibly missing) slot j of cell c stands for."""
         quad = len(self.cells[c]) == 4
         replace = QUAD_REPLACE if quad else TRI_REPLACE
-        while self.slots[c][j][0] == SLOT_MISSING:
-            j = replace[j]
-        return j
+        return self.resolve_partial(self.slots[c], j, replace)
 
     def slot_value_cell(self, c: int, j: int) -> int:
-        """Cell whose average is read for slot j (ghosts and i0 read cell c)."""
-        kind, x, _, _, _ = self.slots[c][self.resolve(c, j)]
-        return x if kind == SLOT_CELL else c
+        """Cell whose average is read for slot j (a mirror image reads the cell it mirrors)."""
+        return self.slots[c][self.resolve(c, j)][1]
+
+    def face_line(self, f: int):
+        """End points of face f as seen from its L cell."""
+        L, k = self.face_L[f], self.face_kL[f]
+        p = self.nodes[self.cells[L]]
+        return p[k], p[(k + 1) % len(p)]
 
     def slot_polygon(self, c: int, j: int) -> np.ndarray:
-        """Vertices (translated or mirrored) of the cell standing in slot j of cell c."""
-        kind, x, sh, _, gf = self.slots[c][self.resolve(c, j)]
-        if kind == SLOT_CELL:
-            return self.nodes[self.cells[x]] + sh
-        p = self.nodes[self.cells[c]]
-        a, b = p[gf], p[(gf + 1) % len(p)]
-        t = (b - a) / np.hypot(*(b - a))
-        r = p - a
-        mirrored = a + 2.0 * (r @ t)[:, None] * t[None, :] - r
-        return mirrored[::-1]
+        """Vertices (translated and/or mirrored) of the cell standing in slot j of cell c."""
+        kind, x, sh, _, refl = self.slots[c][self.resolve(c, j)]
+        p = self.nodes[self.cells[x]] + sh
+        for f in refl:  # mirror across each boundary face line in turn (outflow meshes: no shifts)
+            a, b = self.face_line(f)
+            t = (b - a) / np.hypot(*(b - a))
+            r = p - a
+            p = (a + 2.0 * (r @ t)[:, None] * t[None, :] - r)[::-1]
+        return p
 
 
 def polygon_area_centroid(p: np.ndarray):

@@ -14,10 +14,16 @@
 //  - triangle: i4, i8 = children of i1 at nodes 0, 1; i5, i9 = children of
 //    i2 at nodes 1, 2; i6, i7 = children of i3 at nodes 2, 0.
 //    Replacements: i4..i6 -> i0, i7..i9 -> i4..i6.
-//  - a child is missing (E_j = 0) if it lies across a boundary face, if it
-//    is i0 or a face neighbour, or (second tier) if it is its partner's cell.
-//  - an outflow boundary face gives a ghost face neighbour (the mirror image
-//    of i0, read as i0's own average); ghosts have no children.
+//  - a child is missing (E_j = 0) if it is i0 or a face neighbour, or
+//    (second tier) if it is its partner's cell; members are compared by
+//    (cell, mirror faces).
+//  - outflow boundaries continue the stencil by mirror images: the face
+//    neighbour across a boundary face is i0 mirrored across it; a child
+//    reached through a boundary face of a real face neighbour is that
+//    neighbour mirrored across the face; a child of a mirrored i0 is the
+//    mirror, across the same face, of the member across i0's other face at
+//    that node (two mirrors at a corner).  A mirror image reads the average
+//    of the cell it mirrors (zero-gradient outflow).
 #include "host_mesh.hpp"
 
 #include <algorithm>
@@ -71,39 +77,63 @@ int resolve_slot(const Mesh& m, int64_t c, int j) {
 }
 
 int32_t slot_value_cell(const Mesh& m, int64_t c, int j) {
-  const Slot& s = m.slots[c * kMaxSlots + resolve_slot(m, c, j)];
-  return s.kind == SLOT_CELL ? s.cell : (int32_t)c;
+  return m.slots[c * kMaxSlots + resolve_slot(m, c, j)].cell;
 }
 
 int slot_polygon(const Mesh& m, int64_t c, int j, double out[4][2]) {
   const Slot& s = m.slots[c * kMaxSlots + resolve_slot(m, c, j)];
-  if (s.kind == SLOT_CELL) {
-    const int64_t x = s.cell;
-    const int inst = m.inst[c];
-    const double tx = s.sx * m.inst_period[2 * inst], ty = s.sy * m.inst_period[2 * inst + 1];
-    const int nv = m.nvert[x];
-    for (int i = 0; i < nv; ++i) {
-      out[i][0] = m.verts[(x * 4 + i) * 2] + tx;
-      out[i][1] = m.verts[(x * 4 + i) * 2 + 1] + ty;
-    }
-    return nv;
-  }
-  // ghost: reflect i0 across the line of its face s.face, reversing the order
-  const int nv = m.nvert[c];
-  const double* v = &m.verts[c * 8];
-  const int f = s.face;
-  const double ax = v[2 * f], ay = v[2 * f + 1];
-  const double bx = v[2 * ((f + 1) % nv)], by = v[2 * ((f + 1) % nv) + 1];
-  const double L = std::hypot(bx - ax, by - ay);
-  const double tx = (bx - ax) / L, ty = (by - ay) / L;
+  const int64_t x = s.cell;
+  const int inst = m.inst[c];
+  const double tx = s.sx * m.inst_period[2 * inst], ty = s.sy * m.inst_period[2 * inst + 1];
+  const int nv = m.nvert[x];
+  double p[4][2];
   for (int i = 0; i < nv; ++i) {
-    const double rx = v[2 * i] - ax, ry = v[2 * i + 1] - ay;
-    const double d = rx * tx + ry * ty;
-    out[nv - 1 - i][0] = ax + 2.0 * d * tx - rx;
-    out[nv - 1 - i][1] = ay + 2.0 * d * ty - ry;
+    p[i][0] = m.verts[(x * 4 + i) * 2] + tx;
+    p[i][1] = m.verts[(x * 4 + i) * 2 + 1] + ty;
   }
+  for (int r = 0; r < (s.kind == SLOT_GHOST ? s.nref : 0); ++r) {
+    // reflect across the line of boundary face ref[r] (as seen from its cell), reversing the order
+    const int32_t f = s.ref[r];
+    const int64_t L = m.fL[f];
+    const int k = m.fkL[f], k1 = (k + 1) % m.nvert[L];
+    const double ax = m.verts[L * 8 + 2 * k], ay = m.verts[L * 8 + 2 * k + 1];
+    const double bx = m.verts[L * 8 + 2 * k1], by = m.verts[L * 8 + 2 * k1 + 1];
+    const double len = std::hypot(bx - ax, by - ay);
+    const double ux = (bx - ax) / len, uy = (by - ay) / len;
+    double q[4][2];
+    for (int i = 0; i < nv; ++i) {
+      const double rx = p[i][0] - ax, ry = p[i][1] - ay;
+      const double d = rx * ux + ry * uy;
+      q[nv - 1 - i][0] = ax + 2.0 * d * ux - rx;
+      q[nv - 1 - i][1] = ay + 2.0 * d * uy - ry;
+    }
+    for (int i = 0; i < nv; ++i) { p[i][0] = q[i][0]; p[i][1] = q[i][1]; }
+  }
+  for (int i = 0; i < nv; ++i) { out[i][0] = p[i][0]; out[i][1] = p[i][1]; }
   return nv;
 }
+
+namespace {
+
+Slot cell_slot(int32_t x, int sx, int sy) { return Slot{x, SLOT_CELL, (int8_t)sx, (int8_t)sy, 0, {-1, -1}}; }
+
+// Member across local face k of the real cell c: its neighbour, or c mirrored across the face.
+Slot image_across(const Mesh& m, int64_t c, int k) {
+  const int32_t x = m.nb_cell[c * 4 + k];
+  if (x >= 0) return cell_slot(x, m.nb_sx[c * 4 + k], m.nb_sy[c * 4 + k]);
+  return Slot{(int32_t)c, SLOT_GHOST, 0, 0, 1, {m.cell_face[c * 4 + k], -1}};
+}
+
+bool same_member(const Slot& a, const Slot& b) {
+  if (a.kind == SLOT_MISSING || b.kind == SLOT_MISSING) return false;
+  const int na = a.kind == SLOT_GHOST ? a.nref : 0, nb = b.kind == SLOT_GHOST ? b.nref : 0;
+  if (a.cell != b.cell || na != nb) return false;
+  for (int r = 0; r < na; ++r)
+    if (a.ref[r] != b.ref[r]) return false;
+  return true;
+}
+
+}  // namespace
 
 int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const int64_t* cell_nodes,
                int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], Mesh& out,
@@ -329,39 +359,39 @@ int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const
   }
   m.nF = (int64_t)m.fL.size();
   // ---- 6. stencils
-  m.slots.assign(n_cells * kMaxSlots, Slot{-1, SLOT_MISSING, 0, 0, -1});
+  m.slots.assign(n_cells * kMaxSlots, Slot{-1, SLOT_MISSING, 0, 0, 0, {-1, -1}});
   for (int64_t i = 0; i < n_cells; ++i) {
     Slot* s = &m.slots[i * kMaxSlots];
     const int k_n = m.nvert[i];
-    s[0] = Slot{(int32_t)i, SLOT_CELL, 0, 0, -1};
-    for (int k = 0; k < k_n; ++k) {
-      const int32_t x = m.nb_cell[i * 4 + k];
-      if (x < 0) s[k + 1] = Slot{(int32_t)i, SLOT_GHOST, 0, 0, (int8_t)k};
-      else s[k + 1] = Slot{x, SLOT_CELL, m.nb_sx[i * 4 + k], m.nb_sy[i * 4 + k], -1};
-    }
+    s[0] = cell_slot((int32_t)i, 0, 0);
+    for (int k = 0; k < k_n; ++k) s[k + 1] = image_across(m, i, k);
     const ChildRule* rules = k_n == 4 ? kQuadRules : kTriRules;
     const int n_rules = k_n == 4 ? 8 : 6;
     for (int r = 0; r < n_rules; ++r) {
       const ChildRule& R = rules[r];
       const Slot& parent = s[R.face + 1];
-      int32_t child = -1;
-      int sx = 0, sy = 0;
+      Slot child;
       if (parent.kind == SLOT_CELL) {
         const int32_t p = parent.cell;
         const int kp = m.nb_face[i * 4 + R.face];
         const int np = m.nvert[p];
         const int other = R.start ? (kp + 1) % np : (kp + np - 1) % np;
-        child = m.nb_cell[(int64_t)p * 4 + other];
-        sx = parent.sx + m.nb_sx[(int64_t)p * 4 + other];
-        sy = parent.sy + m.nb_sy[(int64_t)p * 4 + other];
+        const int32_t x = m.nb_cell[(int64_t)p * 4 + other];
+        if (x >= 0)
+          child = cell_slot(x, parent.sx + m.nb_sx[(int64_t)p * 4 + other], parent.sy + m.nb_sy[(int64_t)p * 4 + other]);
+        else
+          child = Slot{p, SLOT_GHOST, parent.sx, parent.sy, 1, {m.cell_face[(int64_t)p * 4 + other], -1}};
+      } else {
+        // parent = i0 mirrored across its face R.face: mirror the member across i0's other face at the node
+        const int k2 = R.start ? (R.face + k_n - 1) % k_n : (R.face + 1) % k_n;
+        child = image_across(m, i, k2);
+        child.kind = SLOT_GHOST;
+        child.ref[child.nref++] = m.cell_face[i * 4 + R.face];
       }
-      bool missing = child < 0 || child == (int32_t)i;
-      for (int k = 1; k <= k_n && !missing; ++k)
-        if (s[k].kind == SLOT_CELL && s[k].cell == child) missing = true;
-      if (!missing && R.partner != 0) {
-        missing = child == slot_value_cell(m, i, R.partner);
-      }
-      if (!missing) s[R.slot] = Slot{child, SLOT_CELL, (int8_t)sx, (int8_t)sy, -1};
+      bool missing = false;
+      for (int k = 0; k <= k_n && !missing; ++k) missing = same_member(child, s[k]);
+      if (!missing && R.partner != 0) missing = same_member(child, s[resolve_slot(m, i, R.partner)]);
+      if (!missing) s[R.slot] = child;
     }
   }
   return WENO_OK;
@@ -408,6 +438,8 @@ int concat_meshes(const Mesh* const* meshes, int32_t n, Mesh& out, std::string& 
       for (int j = 0; j < kMaxSlots; ++j) {
         Slot s = a.slots[c * kMaxSlots + j];
         if (s.kind != SLOT_MISSING) s.cell = g(s.cell);
+        if (s.kind == SLOT_GHOST)
+          for (int r = 0; r < s.nref; ++r) s.ref[r] = (int32_t)(s.ref[r] + offF);
         m.slots[d * kMaxSlots + j] = s;
       }
     }

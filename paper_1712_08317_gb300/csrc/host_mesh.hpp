@@ -15,11 +15,14 @@ enum : int8_t { SLOT_CELL = 0, SLOT_GHOST = 1, SLOT_MISSING = 2 };
 
 constexpr int kMaxSlots = 13;  // i0 .. i12
 
+// A stencil member: a mesh cell, translated by whole periods (periodic meshes)
+// or mirrored across one or two outflow boundary faces (SLOT_GHOST).
 struct Slot {
-  int32_t cell;     // SLOT_CELL: cell id; SLOT_GHOST: the owner i0; SLOT_MISSING: -1
+  int32_t cell;     // the cell whose geometry (and average) the slot carries; -1 when missing
   int8_t kind;
-  int8_t sx, sy;    // SLOT_CELL: translation in periods of the owner's instance
-  int8_t face;      // SLOT_GHOST: local face of i0 the ghost mirrors across
+  int8_t sx, sy;    // translation in periods of the owner's instance
+  int8_t nref;      // SLOT_GHOST: number of mirror faces (1 or 2), applied in order
+  int32_t ref[2];   // SLOT_GHOST: face ids of the boundary faces mirrored across
 };
 
 struct Mesh {
@@ -74,7 +77,7 @@ int resolve_slot(const Mesh& m, int64_t c, int j);
 // Vertices (translated or mirrored) of the cell standing in slot j of c; returns the count.
 int slot_polygon(const Mesh& m, int64_t c, int j, double out[4][2]);
 
-// Cell whose average slot j reads at run time (ghosts and i0 read c).
+// Cell whose average slot j reads at run time (a mirror image reads the cell it mirrors).
 int32_t slot_value_cell(const Mesh& m, int64_t c, int j);
 
 }  // namespace weno

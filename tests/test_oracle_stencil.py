@@ -66,13 +66,18 @@ def _flower(n, quad):
     return OracleMesh(np.array(nodes), ptr, np.array(cells).ravel(), "outflow")
 
 
+def _face(m, c, k):
+    return m.cell_face[c][k]
+
+
 @pytest.mark.parametrize("valence", [3, 4, 5, 6])
 def test_quad_children_at_a_node_of_given_valence(valence):
     m = _flower(valence, quad=True)
     s = m.slots[0]
-    # i1 across O-P0 is the petal before, i4 across P1-O the petal after; i2, i3 are ghosts
+    # i1 across O-P0 is the petal before, i4 across P1-O the petal after; i2, i3 mirror i0
     assert s[1][1] == valence - 1 and s[4][1] == 1
-    assert s[2][0] == SLOT_GHOST and s[3][0] == SLOT_GHOST
+    assert s[2][0] == SLOT_GHOST and s[2][1] == 0 and s[2][4] == (_face(m, 0, 1),)
+    assert s[3][0] == SLOT_GHOST and s[3][1] == 0 and s[3][4] == (_face(m, 0, 2),)
     if valence == 3:
         assert s[5][0] == SLOT_MISSING and m.resolve(0, 5) == 0
         assert s[9][0] == SLOT_MISSING and m.resolve(0, 9) == 0
@@ -81,16 +86,27 @@ def test_quad_children_at_a_node_of_given_valence(valence):
         assert s[9][0] == SLOT_MISSING and m.resolve(0, 9) == 5
     else:
         assert s[5][1] == valence - 2 and s[9][1] == 2 and s[5][3] == s[9][3] == 1
-    # children across boundary faces and of ghosts do not exist
-    for slot in (6, 7, 8, 10, 11, 12):
-        assert s[slot][0] == SLOT_MISSING and m.resolve(0, slot) == 0
+    # across boundary faces the stencil continues with mirror images
+    p1 = valence - 1
+    f_p1 = m.cell_face[p1][2]          # petal p1's face Q_{p1} - P0 lies on the boundary
+    assert s[6][0] == SLOT_GHOST and s[6][1] == p1 and s[6][4] == (f_p1,)
+    assert s[7][0] == SLOT_GHOST and s[7][1] == 0 and s[7][4] == (_face(m, 0, 1), _face(m, 0, 2))
+    assert s[8][0] == SLOT_GHOST and s[8][1] == 1 and s[8][4] == (_face(m, 0, 2),)
+    assert s[10][0] == SLOT_GHOST and s[10][1] == p1 and s[10][4] == (_face(m, 0, 1),)
+    assert s[11][0] == SLOT_GHOST and s[11][1] == 0 and s[11][4] == (_face(m, 0, 2), _face(m, 0, 1))
+    assert s[12][0] == SLOT_GHOST and s[12][1] == 1 and s[12][4] == (m.cell_face[1][1],)
+    # a mirror image is the reflected polygon: the double mirror keeps i0's area
+    poly = m.slot_polygon(0, 7)
+    area = 0.5 * abs(np.sum(poly[:, 0] * np.roll(poly[:, 1], -1) - np.roll(poly[:, 0], -1) * poly[:, 1]))
+    assert area == pytest.approx(m.area[0], rel=1e-13)
 
 
 @pytest.mark.parametrize("valence", [3, 4, 5, 6])
 def test_triangle_children_at_a_node_of_given_valence(valence):
     m = _flower(valence, quad=False)
     s = m.slots[0]
-    assert s[1][1] == valence - 1 and s[3][1] == 1 and s[2][0] == SLOT_GHOST
+    assert s[1][1] == valence - 1 and s[3][1] == 1
+    assert s[2][0] == SLOT_GHOST and s[2][1] == 0 and s[2][4] == (_face(m, 0, 1),)
     if valence == 3:
         assert s[4][0] == SLOT_MISSING and m.resolve(0, 4) == 0
         assert s[7][0] == SLOT_MISSING and m.resolve(0, 7) == 0
@@ -99,8 +115,11 @@ def test_triangle_children_at_a_node_of_given_valence(valence):
         assert s[7][0] == SLOT_MISSING and m.resolve(0, 7) == 4
     else:
         assert s[4][1] == valence - 2 and s[7][1] == 2
-    for slot in (5, 6, 8, 9):
-        assert s[slot][0] == SLOT_MISSING and m.resolve(0, slot) == 0
+    p1 = valence - 1
+    assert s[8][0] == SLOT_GHOST and s[8][1] == p1 and s[8][4] == (m.cell_face[p1][1],)
+    assert s[5][0] == SLOT_GHOST and s[5][1] == p1 and s[5][4] == (_face(m, 0, 1),)
+    assert s[9][0] == SLOT_GHOST and s[9][1] == 1 and s[9][4] == (_face(m, 0, 1),)
+    assert s[6][0] == SLOT_GHOST and s[6][1] == 1 and s[6][4] == (m.cell_face[1][1],)
 
 
 def test_structured_triangles_have_full_stencils():
@@ -153,17 +172,28 @@ def test_children_and_missing_rules_by_brute_force(cfg, kind):
         children = QUAD_CHILDREN if quad else TRI_CHILDREN
         replace = QUAD_REPLACE if quad else TRI_REPLACE
         s = m.slots[c]
-        face_cells = {c} | {s[j][1] for j in range(1, len(m.cells[c]) + 1) if s[j][0] == SLOT_CELL}
+        taken = {(s[j][1], s[j][4]) for j in range(0, len(m.cells[c]) + 1)}
         for j, k, at_start in children:
             if s[k + 1][0] == SLOT_GHOST:
-                raw = -1
-            else:
-                raw = _brute_child(m, c, k, at_start)
-                assert raw == m.child(c, k, at_start)[0]
-            missing = raw < 0 or raw in face_cells
+                # child of a ghost: a mirror image across i0's boundary face k
+                assert s[j][0] in (SLOT_GHOST, SLOT_MISSING)
+                if s[j][0] == SLOT_GHOST:
+                    assert s[j][4][-1] == m.cell_face[c][k]
+                continue
+            raw = _brute_child(m, c, k, at_start)
+            if raw < 0:
+                # the parent's face at that node is a boundary face: the parent's mirror image
+                assert s[j][0] in (SLOT_GHOST, SLOT_MISSING)
+                if s[j][0] == SLOT_GHOST:
+                    assert s[j][1] == s[k + 1][1] and len(s[j][4]) == 1
+                continue
+            assert raw == m.child(c, k, at_start)[0]
+            ident = (raw, ())
+            missing = ident in taken
             r = replace[j]
             if not missing and r != 0:
-                missing = raw == m.slot_value_cell(c, r)
+                pj = s[m.resolve(c, r)]
+                missing = ident == (pj[1], pj[4])
             assert (s[j][0] == SLOT_MISSING) == missing
             if not missing:
                 assert s[j][1] == raw
