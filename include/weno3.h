@@ -203,6 +203,12 @@ int weno_conservation(weno_solver_t s, const void* U, const void* U_lo, double* 
  * non-finite value since the last check.  Synchronising. */
 int weno_check(weno_solver_t s, void* cuda_stream);
 
+/* Per-instance form of weno_check: flags[n_instances] (host) receives 1 for every
+ * instance that had a non-physical Gauss-point state since the last check, 0
+ * otherwise; the flags are cleared.  Returns WENO_OK (or WENO_ETIMEOUT, as
+ * weno_check).  Synchronising. */
+int weno_check_instances(weno_solver_t s, int32_t* flags, void* cuda_stream);
+
 /* Launches one pass of the residual on its own (profiling aid; the kernels
  * are the ones weno_residual and weno_step run):
  *   pass 1: cell reconstruction of U (U_lo) into the solver's Gauss-point scratch

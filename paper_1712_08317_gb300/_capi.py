@@ -52,6 +52,7 @@ SIGNATURES = {
     "weno_max_dt": (C.c_int, [P, P, P, C.c_double, P, P]),
     "weno_conservation": (C.c_int, [P, P, P, P, P]),
     "weno_check": (C.c_int, [P, P]),
+    "weno_check_instances": (C.c_int, [P, P, P]),
     "weno_pass": (C.c_int, [P, C.c_int32, P, P, P]),
     "weno_autotune": (C.c_int, [P, P, P, P]),
     "weno_solver_launch_config": (C.c_int, [P, P]),

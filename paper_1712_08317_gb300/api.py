@@ -203,6 +203,12 @@ class Solver:
         """Launch one pass alone: 1 reconstruction, 2 face fluxes, 3 gather (profiling aid)."""
         capi.check(self._lib.weno_pass(self._h, int(which), self._p(U), self._p(U_lo), self._stream(stream)))
 
+    def check_instances(self, stream=None) -> np.ndarray:
+        """Per-instance non-physical flags since the last check (cleared)."""
+        out = np.zeros(self.n_instances, dtype=np.int32)
+        capi.check(self._lib.weno_check_instances(self._h, _ptr(out), self._stream(stream)))
+        return out
+
     def check(self, stream=None):
         capi.check(self._lib.weno_check(self._h, self._stream(stream)))
 

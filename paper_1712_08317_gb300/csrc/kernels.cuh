@@ -521,13 +521,16 @@ __device__ __forceinline__ void store_vec<double, 4>(double* p, const double w[4
   reinterpret_cast<double2*>(p)[1] = make_double2(w[2], w[3]);
 }
 
+// flag[instance] is set when a Gauss-point state of a face of that instance is
+// non-physical; nQ and inst map the left Gauss-value index back to its cell's
+// instance (inst == nullptr: a single instance).
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_face(
     const T* __restrict__ Wg, const int32_t* __restrict__ gl, const int32_t* __restrict__ gr,
     const T* __restrict__ fnx, const T* __restrict__ fny, const T* __restrict__ flen, int64_t nF,
-    T* __restrict__ F, Prm<T> prm, int* __restrict__ flag) {
-  bool bad = false;
+    T* __restrict__ F, Prm<T> prm, int* __restrict__ flag, const int32_t* __restrict__ inst, int64_t nQ) {
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nF; f += (int64_t)gridDim.x * blockDim.x) {
+    bool bad = false;
     const int64_t il = __ldg(gl + f);
     const int64_t ir = __ldg(gr + f);
     const T nx = __ldg(fnx + f), ny = __ldg(fny + f), len = __ldg(flen + f);
@@ -557,8 +560,11 @@ __global__ void __launch_bounds__(256) k_face(
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] *= T(0.5) * len;
     store_vec<T, NV>(F + f * NV, acc);
+    if (bad) {  // every writer stores the same value
+      const int64_t cl = il < 8 * nQ ? il / 8 : nQ + (il - 8 * nQ) / 6;
+      flag[inst ? __ldg(inst + cl) : 0] = 1;
+    }
   }
-  if (bad) *flag = 1;  // every writer stores the same value
 }
 
 // ---------------------------------------------------------------- K3

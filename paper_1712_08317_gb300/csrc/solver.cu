@@ -192,7 +192,8 @@ void launch_face(S& s, cudaStream_t st) {
   weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
   if (s.nF)
     weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
-        (const T*)s.Wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)s.F, p, s.flag);
+        (const T*)s.Wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)s.F, p, s.flag,
+        s.inst, s.nQ);
 }
 
 template <typename T, int NV, bool COMP, int MODE>
@@ -687,8 +688,8 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   if ((r = d.alloc(&d.dt_dev, sizeof(double) * d.n_inst))) return r;
   if ((r = d.alloc(&d.red, sizeof(double) * d.n_inst * d.nv))) return r;
   if ((r = d.alloc(&d.cell_dt, sizeof(double) * d.N))) return r;
-  if ((r = d.alloc(&d.flag, sizeof(int)))) return r;
-  CK(cudaMemsetAsync(d.flag, 0, sizeof(int), st));
+  if ((r = d.alloc(&d.flag, sizeof(int) * d.n_inst))) return r;
+  CK(cudaMemsetAsync(d.flag, 0, sizeof(int) * d.n_inst, st));
   if ((r = d.alloc(&d.err, sizeof(int)))) return r;
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), st));
   if (!d.fp64 && d.nv == 4 && (r = setup_tma(d))) return r;
@@ -791,14 +792,33 @@ int weno_check(weno_solver_t s, void* cuda_stream) {
   if (!s) return fail(WENO_EINVAL, "null argument");
   DeviceGuard g(s->dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  int h = 0, t = 0;
-  CK(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<int> h(s->n_inst, 0);
+  int t = 0;
+  CK(cudaMemcpyAsync(h.data(), s->flag, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&t, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemsetAsync(s->flag, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(s->flag, 0, sizeof(int) * s->n_inst, st));
   CK(cudaMemsetAsync(s->err, 0, sizeof(int), st));
   CK(cudaStreamSynchronize(st));
   if (t) return fail(WENO_ETIMEOUT, "a bounded wait for a tensor-memory copy gave up; results of that launch are invalid");
-  if (h) return fail(WENO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or non-finite) at a Gauss point");
+  int bad = 0;
+  for (int i = 0; i < s->n_inst; ++i) bad += h[i] != 0;
+  if (bad)
+    return fail(WENO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or non-finite) at a Gauss point in " +
+                                   std::to_string(bad) + " of " + std::to_string(s->n_inst) + " instance(s)");
+  return WENO_OK;
+}
+
+int weno_check_instances(weno_solver_t s, int32_t* flags, void* cuda_stream) {
+  if (!s || !flags) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int t = 0;
+  CK(cudaMemcpyAsync(flags, s->flag, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&t, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemsetAsync(s->flag, 0, sizeof(int) * s->n_inst, st));
+  CK(cudaMemsetAsync(s->err, 0, sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  if (t) return fail(WENO_ETIMEOUT, "a bounded wait for a tensor-memory copy gave up; results of that launch are invalid");
   return WENO_OK;
 }
 
@@ -939,7 +959,8 @@ void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void*
   weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
   if (s.nF)
     weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
-        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag);
+        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
+        s.inst, s.nQ);
   if (s.nQ)
     weno::dev::k_gather<T, NV, 4, COMP, 0><<<grid_of(s.k3q, s.nQ), s.k3q.block, 0, st>>>(
         (const T*)fl, s.q_cf, (const T*)s.inv_area, (const T*)s.inv_area_lo, s.nQ, 0, nullptr, nullptr, nullptr,

@@ -188,6 +188,23 @@ def test_nonphysical_state_is_reported_and_cleared():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_nonphysical_flags_name_the_instance(precision):
+    mi, W, _ = _oracle("euler-mixed")
+    m = Mesh.from_input(mi)
+    big = Solver(Mesh.concat([m, m, m]), eqn="euler", precision=precision)
+    Wcat = np.concatenate([W, W, W], axis=1)
+    Wcat[3, W.shape[1] + 17] = -0.5       # negative energy in one cell of instance 1
+    U, Ul = big.to_device(Wcat)
+    big.residual(U, Ul)
+    assert big.check_instances().tolist() == [0, 1, 0]
+    assert big.check_instances().tolist() == [0, 0, 0]   # cleared
+    big.residual(U, Ul)
+    with pytest.raises(_capi.WenoError) as e:
+        big.check()
+    assert e.value.code == _capi.WENO_ENONPHYS and "1 of 3" in str(e.value)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_autotune_does_not_change_results(precision):
     mi, W, _ = _oracle("euler-mixed")
     sol = Solver(Mesh.from_input(mi), eqn="euler", precision=precision)
