@@ -217,52 +217,68 @@ def k1_bytes(nQ, nT, nv, esz, comp):
     return nQ * per(12, 8) + nT * per(9, 6)
 
 
-def run_accuracy(args):
-    """Convergence ladders to t = 2 through the CUDA path: FP64 and FP32C, L1 / Linf of rho vs exact."""
+def _cell_areas(mi):
+    cells, cnt = mi.padded_cells()
+    P = mi.nodes[cells]
+    x, y = P[..., 0], P[..., 1]
+    return 0.5 * np.abs((x * np.roll(y, -1, 1) - np.roll(x, -1, 1) * y).sum(1))  # padded vertex repeats add 0
+
+
+ACC_FAMILIES = {
+    "densitywave-tri": (lambda n: __import__("synthetic").mesh_for_config(2, n=n, seed=0, kind="tri"), "density_wave"),
+    "vortex-lowq": (lambda n: __import__("synthetic").stretched_vortex_mesh(n, seed=0), "isentropic_vortex"),
+}
+
+
+def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0):
+    """One mesh of a convergence ladder run to t = T through the CUDA path: L1 / Linf of rho vs exact."""
     import torch
     import synthetic as S
     from paper_1712_08317_gb300.api import Mesh, Solver
-    fams = {
-        "densitywave-tri": (lambda n: S.mesh_for_config(2, n=n, seed=0, kind="tri"), S.density_wave,
-                            [int(x) for x in args.ladder_dw.split(",")]),
-        "vortex-lowq": (lambda n: S.stretched_vortex_mesh(n, seed=0), S.isentropic_vortex,
-                        [int(x) for x in args.ladder_vortex.split(",")]),
-    }
+    mk, fname = ACC_FAMILIES[family]
+    f = getattr(S, fname)
+    mi = mk(n)
+    mesh = Mesh.from_input(mi)
+    W0 = S.cell_average(mi, f)
+    ex = S.cell_average(mi, lambda x, y: f(x, y, T))
+    area = _cell_areas(mi)
+    row = {"n": n, "cells": mi.n_cells}
+    for prec in precisions:
+        sol = Solver(mesh, eqn="euler", precision=prec, eps=eps)
+        U, Ul = sol.to_device(W0)
+        dt0 = float(sol.max_dt(U, Ul, cfl)[0])
+        steps = int(np.ceil(T / dt0 - 1e-12))
+        dt = T / steps
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            sol.step(U, Ul, dt)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        try:
+            sol.check()
+        except Exception as exc:  # non-physical state: record it, keep the ladder going
+            row[prec] = {"steps": steps, "failed": str(exc).split(":")[0], "seconds": el}
+            continue
+        e = np.abs(sol.to_host(U, Ul)[0] - ex[0])
+        row[prec] = {"steps": steps, "l1": float((e * area).sum() / area.sum()), "linf": float(e.max()),
+                     "seconds": el}
+    if "l1" in row.get("fp32c", {}) and "l1" in row.get("fp64", {}):
+        row["l1_fp32c_over_fp64"] = row["fp32c"]["l1"] / row["fp64"]["l1"]
+    return row
+
+
+def run_accuracy(args):
+    """Convergence ladders to t = 2 through the CUDA path: FP64 and FP32C, L1 / Linf of rho vs exact."""
+    ladders = {"densitywave-tri": [int(x) for x in args.ladder_dw.split(",")],
+               "vortex-lowq": [int(x) for x in args.ladder_vortex.split(",")]}
     T = 2.0
     out = {}
-    for name, (mk, f, ladder) in fams.items():
+    for name, ladder in ladders.items():
         if name not in args.families.split(","):
             continue
         rows = []
         for n in ladder:
-            mi = mk(n)
-            mesh = Mesh.from_input(mi)
-            W0 = S.cell_average(mi, f)
-            ex = S.cell_average(mi, lambda x, y: f(x, y, T))
-            cells, cnt = mi.padded_cells()
-            P = mi.nodes[cells]
-            x, y = P[..., 0], P[..., 1]
-            area = 0.5 * np.abs((x * np.roll(y, -1, 1) - np.roll(x, -1, 1) * y).sum(1))
-            row = {"n": n, "cells": mi.n_cells}
-            for prec in args.precisions.split(","):
-                sol = Solver(mesh, eqn="euler", precision=prec, eps=args.eps)
-                U, Ul = sol.to_device(W0)
-                dt0 = float(sol.max_dt(U, Ul, args.cfl)[0])
-                steps = int(np.ceil(T / dt0 - 1e-12))
-                dt = T / steps
-                t0 = time.perf_counter()
-                for _ in range(steps):
-                    sol.step(U, Ul, dt)
-                torch.cuda.synchronize()
-                el = time.perf_counter() - t0
-                try:
-                    sol.check()
-                except Exception as exc:  # non-physical state: record it, keep the ladder going
-                    row[prec] = {"steps": steps, "failed": str(exc).split(":")[0], "seconds": el}
-                    continue
-                e = np.abs(sol.to_host(U, Ul)[0] - ex[0])
-                row[prec] = {"steps": steps, "l1": float((e * area).sum() / area.sum()), "linf": float(e.max()),
-                             "seconds": el}
+            row = ladder_point(name, n, args.precisions.split(","), args.eps, args.cfl, T)
             rows.append(row)
             print(json.dumps({"family": name, **row}), flush=True)
         for prec in args.precisions.split(","):
@@ -272,9 +288,6 @@ def run_accuracy(args):
                 r = (b["cells"] / a["cells"]) ** 0.5
                 b[prec]["order_l1"] = float(np.log(a[prec]["l1"] / b[prec]["l1"]) / np.log(r))
                 b[prec]["order_linf"] = float(np.log(a[prec]["linf"] / b[prec]["linf"]) / np.log(r))
-        for r in rows:
-            if "l1" in r.get("fp32c", {}) and "l1" in r.get("fp64", {}):
-                r["l1_fp32c_over_fp64"] = r["fp32c"]["l1"] / r["fp64"]["l1"]
         out[name] = rows
     print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "eps": args.eps}), flush=True)
 
@@ -292,6 +305,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched leg (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--accuracy", action="store_true", help="convergence ladders to t = 2 instead of the timing run")
+    ap.add_argument("--acc-n", type=int, default=160, help="density-wave mesh of the t = 2 accuracy block (0: skip)")
     ap.add_argument("--ladder-dw", default="20,40,80,160,320")
     ap.add_argument("--ladder-vortex", default="40,80,160")
     ap.add_argument("--eps", type=float, default=1e-6, help="epsilon of the nonlinear weights (accuracy mode)")
@@ -450,18 +464,19 @@ def main():
         W32 = sol.to_host(U, Ul)
         W64 = sol64.to_host(V)
         ex = S.cell_average(mi, lambda x, y: S.isentropic_vortex(x, y, t_fp32), order=4)
-        # cell areas from the mesh input: shoelace over the cell polygons
-        cells, cnt = mi.padded_cells()
-        P = mi.nodes[cells]
-        x, y = P[..., 0], P[..., 1]
-        a = 0.5 * np.abs((x * np.roll(y, -1, 1) - np.roll(x, -1, 1) * y).sum(1))  # padded vertex repeats add 0
-        area = a
+        area = _cell_areas(mi)
 
         def l1(d):
             return float((np.abs(d[0]) * area).sum() / area.sum())
         acc = {"t": t_fp32, "steps": steps_done, "dt": dt, "l1_rho_fp32c_vs_exact": l1(W32 - ex),
                "l1_rho_fp64_vs_exact": l1(W64 - ex), "l1_rho_fp32c_vs_fp64": l1(W32 - W64),
                "conservation_rel_drift_fp32c": float(np.abs(c_end - c_start).max() / np.abs(c_start).max())}
+
+    # accuracy to t = 2 on the density-wave mesh of 51,200 split triangles (FP64 vs FP32C vs exact)
+    acc_t2 = None
+    if rank == 0 and args.acc_n > 0:
+        acc_t2 = {"family": "densitywave-tri", "t": 2.0, "cfl": 0.5,
+                  **ladder_point("densitywave-tri", args.acc_n, ["fp64", "fp32c"])}
 
     launches_per_step = 1 + 3 * ((1 if nQ else 0) + (1 if nT else 0) + 1 + (1 if nQ else 0) + (1 if nT else 0))
     launch_cfg = sol.launch_config().tolist()
@@ -494,6 +509,7 @@ def main():
                      "fp32c_over_fp64": value / fp64_value},
             "batched": batched,
             "accuracy": acc,
+            "accuracy_t2": acc_t2,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

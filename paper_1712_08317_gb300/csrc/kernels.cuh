@@ -156,7 +156,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 #ifndef WENO_K1_MIN_BLOCKS
-#define WENO_K1_MIN_BLOCKS 2  // resident 256-thread blocks per SM the register budget is sized for
+#define WENO_K1_MIN_BLOCKS 2  // resident 256-thread blocks' worth of threads per SM the register budget is sized for
 #endif
 
 // Paired FP32 arithmetic (Blackwell f32x2): candidates j = 2k, 2k+1 share one
@@ -165,24 +165,30 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 rcp2(float2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
 __device__ __forceinline__ float2 abs2(float2 x) { return make_float2(fabsf(x.x), fabsf(x.y)); }
 
+// Per-candidate quantities of one (cell, variable) that do not depend on the
+// Gauss point, as candidate pairs: gradient (gx, gy), beta and be = beta + eps.
+template <int P>
+struct CandPairs {
+  float2 gx[P], gy[P], b[P], be[P];
+};
+
 // Increment R(x_G) - W0 of one Gauss point (Section 3.4, FP32) from the
-// candidates' gradient pairs (gx, gy), beta, beta + eps, and the split linear
-// weights gamma+ (gpos), gamma- (gneg) with their sums sigma+- (sp, sm), which
-// depend on geometry only and are precomputed in FP64:
+// candidate pairs and the split linear weights gamma+ (gpos), gamma- (gneg)
+// with their sums sigma+- (sp, sm), which depend on geometry only and are
+// precomputed in FP64:
 //   R - W0 = sigma+ sum delta+ p - sigma- sum delta- p,
 //   delta+-_j = alpha+-_j / sum alpha+-, alpha+-_j = gamma+-_j / (beta~+-_j + eps)^2,
 //   beta~+-_j = beta_j (1 + q + q^2), q = gamma+-_j beta_j.
 // The linear scheme is R - W0 = sum gamma_j p_j = sigma+ sum gamma+ p - sigma- sum gamma- p.
 template <int P>
-__device__ __forceinline__ float gauss_increment(const float2* gx, const float2* gy, const float2* b, float eps,
-                                                 const float2* gpos, const float2* gneg, float dx, float dy, float sp,
-                                                 float sm, int linear) {
-  const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy), eps2 = f2(eps, eps);
+__device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const float2* gpos, const float2* gneg,
+                                                 float dx, float dy, float sp, float sm, int linear) {
+  const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy);
   if (linear) {
     float2 ap = f2(0.f, 0.f), an = f2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-      const float2 p = __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2));
+      const float2 p = __ffma2_rn(c.gx[k], dx2, __fmul2_rn(c.gy[k], dy2));
       ap = __ffma2_rn(gpos[k], p, ap);
       an = __ffma2_rn(gneg[k], p, an);
     }
@@ -191,11 +197,10 @@ __device__ __forceinline__ float gauss_increment(const float2* gx, const float2*
   float2 Ap = f2(0.f, 0.f), Bp = f2(0.f, 0.f), Am = f2(0.f, 0.f), Bm = f2(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    const float2 p = __ffma2_rn(gx[k], dx2, __fmul2_rn(gy[k], dy2));  // P^1_j(x_G) - W0
-    const float2 qp = __fmul2_rn(gpos[k], b[k]), qn = __fmul2_rn(gneg[k], b[k]);
-    const float2 be = __fadd2_rn(b[k], eps2);
-    const float2 bp = __ffma2_rn(b[k], __ffma2_rn(qp, qp, qp), be);
-    const float2 bn = __ffma2_rn(b[k], __ffma2_rn(qn, qn, qn), be);
+    const float2 p = __ffma2_rn(c.gx[k], dx2, __fmul2_rn(c.gy[k], dy2));  // P^1_j(x_G) - W0
+    const float2 qp = __fmul2_rn(gpos[k], c.b[k]), qn = __fmul2_rn(gneg[k], c.b[k]);
+    const float2 bp = __ffma2_rn(c.b[k], __ffma2_rn(qp, qp, qp), c.be[k]);
+    const float2 bn = __ffma2_rn(c.b[k], __ffma2_rn(qn, qn, qn), c.be[k]);
     const float2 ap = __fmul2_rn(gpos[k], rcp2(__fmul2_rn(bp, bp)));
     const float2 an = __fmul2_rn(gneg[k], rcp2(__fmul2_rn(bn, bn)));
     Ap = __fadd2_rn(Ap, ap);
@@ -212,8 +217,8 @@ template <int NV, int M>
 __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, const float* __restrict__ Ulo,
                                                const int32_t* __restrict__ slot, int64_t slot_pitch,
                                                const float4* __restrict__ gop4, int64_t pitch, int64_t q, int64_t c,
-                                               int v, float a0, float& w0, float& l0, float2* gx2, float2* gy2,
-                                               float2* b2) {
+                                               int v, float a0, float eps, float& w0, float& l0,
+                                               CandPairs<(M + 1) / 2>& cp) {
   w0 = __ldg(U + c * NV + v);
   l0 = __ldg(Ulo + c * NV + v);
   float dW[M + 1];
@@ -235,9 +240,11 @@ __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, cons
   if (M % 2) { gx[M] = 0.f; gy[M] = 0.f; b[M] = 0.f; }
 #pragma unroll
   for (int k = 0; k < (M + 1) / 2; ++k) {
-    gx2[k] = f2(gx[2 * k], gx[2 * k + 1]);
-    gy2[k] = f2(gy[2 * k], gy[2 * k + 1]);
-    b2[k] = f2(b[2 * k], b[2 * k + 1]);
+    cp.gx[k] = f2(gx[2 * k], gx[2 * k + 1]);
+    cp.gy[k] = f2(gy[2 * k], gy[2 * k + 1]);
+    const float2 bb = f2(b[2 * k], b[2 * k + 1]);
+    cp.b[k] = bb;
+    cp.be[k] = __fadd2_rn(bb, f2(eps, eps));
   }
 }
 
@@ -257,8 +264,8 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
     const int v = (int)(t - q * NV);
     const int64_t c = first + q;
     float w0, l0;
-    float2 gx[P], gy[P], b[P];
-    cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), w0, l0, gx, gy, b);
+    CandPairs<P> cp;
+    cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
     float* out = Wg + (gbase + q * G) * NV + v;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
@@ -276,14 +283,14 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
         gp[P - 1] = f2(e.x, 0.f);
         gn[P - 1] = f2(e.y, 0.f);
       }
-      const float incr = gauss_increment<P>(gx, gy, b, eps, gp, gn, d.x, d.y, d.z, d.w, linear);
+      const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
       out[(int64_t)g * NV] = w0 + (l0 + incr);
     }
   }
 }
 
 // ---------------------------------------------------------------- K1 with TMA-staged tables
-// Persistent kernel, Euler FP32C: a tile is 64 consecutive cells of one type,
+// Euler FP32C, one block per tile or persistent: a tile is TILE consecutive cells of one type,
 // one (cell, variable) per thread.  One elected thread loads the tile's split
 // linear weights and Gauss offsets into shared memory with 2D TMA copies
 // (cp.async.bulk.tensor) completing on an mbarrier; the stencil gathers of the
@@ -323,13 +330,19 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+#ifndef WENO_K1_TILE
+#define WENO_K1_TILE 16  // cells per block tile of the TMA reconstruction (8, 16, 32 or 64)
+#endif
+static_assert(WENO_K1_TILE == 8 || WENO_K1_TILE == 16 || WENO_K1_TILE == 32 || WENO_K1_TILE == 64, "tile of 8, 16, 32 or 64 cells");
+
 #ifndef WENO_K1_STAGES
 #define WENO_K1_STAGES 1  // shared-memory table buffers per block (2: prefetch the next tile while computing)
 #endif
 
 template <int M, int G>
 struct TmaTile {
-  static constexpr int TILE = 64;  // cells per tile: 256 threads = 64 cells x 4 variables
+  static constexpr int TILE = WENO_K1_TILE;  // cells per tile; TILE x 4 threads (one per variable)
+  static constexpr int THREADS = TILE * 4;
   static constexpr int M4 = M / 4;
   static constexpr int GPM = G * 2 * M4 * TILE * 16;          // gamma+ rows then gamma- rows
   static constexpr int DGS = G * TILE * 16;                    // (x_G - c0, sigma+, sigma-)
@@ -340,7 +353,7 @@ struct TmaTile {
 };
 
 template <int M, int G>
-__global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
+__global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WENO_K1_TILE) k_reconstruct_tma(
     const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
     const __grid_constant__ CUtensorMap map_g1, const float* __restrict__ U, const float* __restrict__ Ulo,
     const int32_t* __restrict__ slot, const float4* __restrict__ gop4, const float* __restrict__ area, int64_t N,
@@ -380,10 +393,10 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
     const int v = tid & 3;
     // the stencil gathers do not depend on the staged tables: start them before waiting
     float w0 = 0.f, l0 = 0.f;
-    float2 gx[P], gy[P], b[P];
+    CandPairs<P> cp;
     if (q < N) {
       const int64_t c = first + q;
-      cell_gradients<4, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), w0, l0, gx, gy, b);
+      cell_gradients<4, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
     }
     const bool ok = mbar_wait_bounded(&bar[st], phase[st]);
     phase[st] ^= 1u;
@@ -418,7 +431,7 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_tma(
           gp[P - 1] = f2(e.x, 0.f);
           gn[P - 1] = f2(e.y, 0.f);
         }
-        const float incr = gauss_increment<P>(gx, gy, b, eps, gp, gn, d.x, d.y, d.z, d.w, linear);
+        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
         out[(int64_t)g * 4] = w0 + (l0 + incr);
       }
     }
@@ -682,28 +695,12 @@ __global__ void k_cell_dt(const T* __restrict__ U, const T* __restrict__ Ulo, co
   }
 }
 
-// One block per instance: deterministic min / sums over the instance's quad
-// range [q0, q1) and triangle range [t0, t1).  mode 0: min of x[c];
-// mode 1: sums of area[c] * (U + U_lo)[c][v] for every v.
-template <typename T, int NV, bool COMP>
-__global__ void k_instance_reduce(const double* __restrict__ x, const T* __restrict__ U, const T* __restrict__ Ulo,
-                                  const double* __restrict__ area, const int64_t* __restrict__ ranges, int mode,
-                                  double* __restrict__ out) {
+// Deterministic reductions in two levels with a fixed partition, so results do
+// not depend on scheduling.  Level 1: one block per chunk [c0, c1) of cells of
+// one instance; mode 0: min of x[c]; mode 1: sums of area[c] * (U + U_lo)[c][v].
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double acc[NV], int mode, double* __restrict__ out) {
   __shared__ double sh[256 * NV];
-  const int inst = blockIdx.x;
-  const int64_t r[4] = {ranges[4 * inst], ranges[4 * inst + 1], ranges[4 * inst + 2], ranges[4 * inst + 3]};
-  double acc[NV];
-  for (int v = 0; v < NV; ++v) acc[v] = mode == 0 ? 1e300 : 0.0;
-  for (int part = 0; part < 2; ++part) {
-    for (int64_t c = r[2 * part] + threadIdx.x; c < r[2 * part + 1]; c += blockDim.x) {
-      if (mode == 0) {
-        acc[0] = fmin(acc[0], x[c]);
-      } else {
-        for (int v = 0; v < NV; ++v)
-          acc[v] += area[c] * ((double)U[c * NV + v] + (COMP ? (double)Ulo[c * NV + v] : 0.0));
-      }
-    }
-  }
   for (int v = 0; v < NV; ++v) sh[v * 256 + threadIdx.x] = acc[v];
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
@@ -715,9 +712,43 @@ __global__ void k_instance_reduce(const double* __restrict__ x, const T* __restr
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    if (mode == 0) out[inst] = sh[0];
-    else for (int v = 0; v < NV; ++v) out[inst * NV + v] = sh[v * 256];
+    if (mode == 0) out[0] = sh[0];
+    else for (int v = 0; v < NV; ++v) out[v] = sh[v * 256];
   }
+}
+
+template <typename T, int NV, bool COMP>
+__global__ void __launch_bounds__(256) k_chunk_reduce(const double* __restrict__ x, const T* __restrict__ U,
+                                                      const T* __restrict__ Ulo, const double* __restrict__ area,
+                                                      const int64_t* __restrict__ chunks, int mode,
+                                                      double* __restrict__ partial) {
+  const int64_t c0 = chunks[2 * blockIdx.x], c1 = chunks[2 * blockIdx.x + 1];
+  double acc[NV];
+  for (int v = 0; v < NV; ++v) acc[v] = mode == 0 ? 1e300 : 0.0;
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    if (mode == 0) {
+      acc[0] = fmin(acc[0], x[c]);
+    } else {
+      for (int v = 0; v < NV; ++v)
+        acc[v] += area[c] * ((double)U[c * NV + v] + (COMP ? (double)Ulo[c * NV + v] : 0.0));
+    }
+  }
+  block_reduce_store<NV>(acc, mode, partial + (int64_t)blockIdx.x * (mode == 0 ? 1 : NV));
+}
+
+// Level 2: one block per instance over its chunks' partials [k0, k1).
+template <int NV>
+__global__ void __launch_bounds__(256) k_instance_reduce(const double* __restrict__ partial,
+                                                         const int64_t* __restrict__ chunk_off, int mode,
+                                                         double* __restrict__ out) {
+  const int inst = blockIdx.x;
+  const int64_t k0 = chunk_off[inst], k1 = chunk_off[inst + 1];
+  const int w = mode == 0 ? 1 : NV;
+  double acc[NV];
+  for (int v = 0; v < NV; ++v) acc[v] = mode == 0 ? 1e300 : 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+    for (int v = 0; v < w; ++v) acc[v] = mode == 0 ? fmin(acc[v], partial[k]) : acc[v] + partial[k * NV + v];
+  block_reduce_store<NV>(acc, mode, out + (int64_t)inst * w);
 }
 
 __global__ void k_fill(double* __restrict__ p, double v, int n) {

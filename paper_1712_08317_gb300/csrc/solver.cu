@@ -54,9 +54,10 @@ unsigned grid_of(const Launch& l, int64_t work) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 0x7fffffff));
 }
 
-// Persistent TMA reconstruction: 256 threads per block, one 64-cell tile per iteration.
+// TMA reconstruction: TILE x 4 threads per block, one TILE-cell tile per iteration.
+constexpr int kTile = weno::dev::TmaTile<12, 8>::TILE;
 unsigned tma_grid(const Launch& l, int64_t cells) {
-  const int64_t tiles = (cells + 63) / 64;
+  const int64_t tiles = (cells + kTile - 1) / kTile;
   const int64_t g = l.grid > 0 ? std::min<int64_t>(l.grid, tiles) : tiles;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 0x7fffffff));
 }
@@ -96,7 +97,9 @@ struct weno_solver_s {
   void *fnx = nullptr, *fny = nullptr, *flen = nullptr;
   double *fnx64 = nullptr, *fny64 = nullptr, *flen64 = nullptr;
   int32_t* inst = nullptr;
-  int64_t* ranges = nullptr;
+  int64_t *chunks = nullptr, *chunk_off = nullptr;  // reduction partition: [begin, end) pairs; per-instance offsets
+  int64_t n_chunks = 0;
+  double* partial = nullptr;
   // scratch
   void *Wg = nullptr, *F = nullptr, *Ws = nullptr, *Wslo = nullptr;
   double *dt_dev = nullptr, *red = nullptr, *cell_dt = nullptr;
@@ -150,11 +153,11 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
       using TQ = weno::dev::TmaTile<12, 8>;
       using TT = weno::dev::TmaTile<9, 6>;
       if (s.nQ && (which & 1))
-        weno::dev::k_reconstruct_tma<12, 8><<<tma_grid(s.k1q, s.nQ), 256, TQ::SMEM, st>>>(
+        weno::dev::k_reconstruct_tma<12, 8><<<tma_grid(s.k1q, s.nQ), TQ::THREADS, TQ::SMEM, st>>>(
             s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
             s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err);
       if (s.nT && (which & 2))
-        weno::dev::k_reconstruct_tma<9, 6><<<tma_grid(s.k1t, s.nT), 256, TT::SMEM, st>>>(
+        weno::dev::k_reconstruct_tma<9, 6><<<tma_grid(s.k1t, s.nT), TT::THREADS, TT::SMEM, st>>>(
             s.t_map_gpm, s.t_map_dgs, s.t_map_g1, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
             s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err);
       return;
@@ -259,8 +262,10 @@ void launch_cell_dt(S& s, const void* U, const void* Ulo, cudaStream_t st) {
 
 template <typename T, int NV, bool COMP>
 void launch_reduce(S& s, const void* U, const void* Ulo, int mode, cudaStream_t st) {
-  weno::dev::k_instance_reduce<T, NV, COMP><<<s.n_inst, 256, 0, st>>>(s.cell_dt, (const T*)U, (const T*)Ulo,
-                                                                       s.area64, s.ranges, mode, s.red);
+  if (s.n_chunks)
+    weno::dev::k_chunk_reduce<T, NV, COMP><<<(unsigned)s.n_chunks, 256, 0, st>>>(
+        s.cell_dt, (const T*)U, (const T*)Ulo, s.area64, s.chunks, mode, s.partial);
+  weno::dev::k_instance_reduce<NV><<<s.n_inst, 256, 0, st>>>(s.partial, s.chunk_off, mode, s.red);
 }
 
 int check_launch() {
@@ -383,13 +388,13 @@ int setup_tma(S& s) {
   int r;
   // rows: gamma+-: G * 2 * (M/4) float4 rows; (x_G - c0, sigma+-): G float4 rows; triangle extras: G float2 rows
   if (s.nQ) {
-    if ((r = make_map_2d(enc, &s.q_map_gpm, s.q_gam, 4 * s.q_pitch, 8 * 6, 16 * s.q_pitch, 256, 8 * 6))) return r;
-    if ((r = make_map_2d(enc, &s.q_map_dgs, s.q_dg, 4 * s.q_pitch, 8, 16 * s.q_pitch, 256, 8))) return r;
+    if ((r = make_map_2d(enc, &s.q_map_gpm, s.q_gam, 4 * s.q_pitch, 8 * 6, 16 * s.q_pitch, 4 * kTile, 8 * 6))) return r;
+    if ((r = make_map_2d(enc, &s.q_map_dgs, s.q_dg, 4 * s.q_pitch, 8, 16 * s.q_pitch, 4 * kTile, 8))) return r;
   }
   if (s.nT) {
-    if ((r = make_map_2d(enc, &s.t_map_gpm, s.t_gam, 4 * s.t_pitch, 6 * 4, 16 * s.t_pitch, 256, 6 * 4))) return r;
-    if ((r = make_map_2d(enc, &s.t_map_dgs, s.t_dg, 4 * s.t_pitch, 6, 16 * s.t_pitch, 256, 6))) return r;
-    if ((r = make_map_2d(enc, &s.t_map_g1, s.t_gam1, 2 * s.t_pitch, 6, 8 * s.t_pitch, 128, 6))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_gpm, s.t_gam, 4 * s.t_pitch, 6 * 4, 16 * s.t_pitch, 4 * kTile, 6 * 4))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_dgs, s.t_dg, 4 * s.t_pitch, 6, 16 * s.t_pitch, 4 * kTile, 6))) return r;
+    if ((r = make_map_2d(enc, &s.t_map_g1, s.t_gam1, 2 * s.t_pitch, 6, 8 * s.t_pitch, 2 * kTile, 6))) return r;
   }
   CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TQ::SMEM));
   CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM));
@@ -673,7 +678,21 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
       ranges[4 * i + part + 1] = c + 1;
     }
     for (auto& x : ranges) if (x < 0) x = 0;
-    if ((r = upload(d, &d.ranges, ranges, st))) return r;
+    // fixed partition of each instance's quad and triangle ranges into chunks (deterministic reductions)
+    constexpr int64_t kChunk = 8192;
+    std::vector<int64_t> chunks, chunk_off(1, 0);
+    for (int i = 0; i < d.n_inst; ++i) {
+      for (int part = 0; part < 2; ++part)
+        for (int64_t c = ranges[4 * i + 2 * part]; c < ranges[4 * i + 2 * part + 1]; c += kChunk) {
+          chunks.push_back(c);
+          chunks.push_back(std::min(c + kChunk, ranges[4 * i + 2 * part + 1]));
+        }
+      chunk_off.push_back((int64_t)chunks.size() / 2);
+    }
+    d.n_chunks = (int64_t)chunks.size() / 2;
+    if ((r = upload(d, &d.chunks, chunks, st))) return r;
+    if ((r = upload(d, &d.chunk_off, chunk_off, st))) return r;
+    if ((r = d.alloc(&d.partial, sizeof(double) * std::max<int64_t>(1, d.n_chunks) * d.nv))) return r;
     if (d.n_inst > 1) {
       if ((r = upload(d, &d.inst, m.inst, st))) return r;
     }
@@ -843,8 +862,8 @@ int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_s
   std::vector<Launch> generic, tma;
   for (int b : blocks)
     for (int w : waves) generic.push_back(Launch{b, w == 0 ? 0 : w * s->nsm * std::max(1, 2048 / b)});
-  // TMA reconstruction: 256 threads; 1-4 blocks per SM (persistent), or one block per tile
-  for (int w : {0, 1, 2, 3, 4}) tma.push_back(Launch{256, w * s->nsm});
+  // TMA reconstruction: TILE x 4 threads; 1-4 blocks of 256 threads per SM (persistent), or one block per tile
+  for (int w : {0, 1, 2, 3, 4}) tma.push_back(Launch{weno::dev::TmaTile<12, 8>::THREADS, w * s->nsm * (64 / kTile)});
   auto tune = [&](Launch& L, auto run, const std::vector<Launch>& cands) -> int {
     float best = 1e30f;
     Launch bestL = L;
