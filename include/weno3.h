@@ -54,7 +54,9 @@ typedef enum {
   WENO_ENOMEM = -4,    /* host or device allocation failed                          */
   WENO_ECUDA = -5,     /* a CUDA runtime call failed (message in weno_last_error)   */
   WENO_ENONPHYS = -6,  /* rho <= 0, p <= 0 or a non-finite value seen at a Gauss point */
-  WENO_ETIMEOUT = -7   /* reserved: a bounded device wait gave up                   */
+  WENO_ETIMEOUT = -7   /* a bounded device wait (FP32C Euler reconstruction: the copy of
+                          a tile's weight tables into shared memory) gave up; results of
+                          the launches since the last check are invalid                */
 } weno_status;
 
 typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_OUTFLOW = 1 } weno_bc_kind;
@@ -198,9 +200,13 @@ int weno_max_dt(weno_solver_t s, const void* U, const void* U_lo, double cfl, do
  * sums[n_instances * n_v] on the host.  Deterministic order. Synchronising. */
 int weno_conservation(weno_solver_t s, const void* U, const void* U_lo, double* sums, void* cuda_stream);
 
-/* Reads and clears the device non-physical-state flag raised by residual /
- * step launches: WENO_ENONPHYS if any Gauss point had rho <= 0, p <= 0 or a
- * non-finite value since the last check.  Synchronising. */
+/* Reads and clears the device flags raised by residual / step launches since
+ * the last check: WENO_ETIMEOUT if a bounded device wait gave up, else
+ * WENO_ENONPHYS if any Gauss point had rho <= 0, p <= 0 or a non-finite value
+ * (weno_last_error names how many instances), else WENO_OK.  The scheme has
+ * no positivity limiter (Section 3.4 gives none), so a state can leave the
+ * physical set; the flag reports it and the launches keep running.
+ * Synchronising. */
 int weno_check(weno_solver_t s, void* cuda_stream);
 
 /* Per-instance form of weno_check: flags[n_instances] (host) receives 1 for every
@@ -226,6 +232,15 @@ int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_s
 /* Current launch configuration: cfg[6] = {cell block, cell grid, face block,
  * face grid, gather block, gather grid}. */
 int weno_solver_launch_config(weno_solver_t s, int32_t* cfg);
+
+/* Testing aid for the bounded device waits (the paper has no counterpart).
+ * With on != 0, the FP32C Euler reconstruction initialises its table-copy
+ * barriers for one arrival more than any thread makes, so every block's wait
+ * runs out after its 1 s limit, the block records the timeout and exits, and
+ * the next weno_check returns WENO_ETIMEOUT; results of those launches are
+ * invalid.  on = 0 restores normal operation.  Step graphs are rebuilt.
+ * WENO_EINVAL for solvers without such waits (FP64, scalar). */
+int weno_solver_debug_stall(weno_solver_t s, int32_t on);
 
 void weno_solver_destroy(weno_solver_t s);
 

@@ -203,6 +203,10 @@ class Solver:
         """Launch one pass alone: 1 reconstruction, 2 face fluxes, 3 gather (profiling aid)."""
         capi.check(self._lib.weno_pass(self._h, int(which), self._p(U), self._p(U_lo), self._stream(stream)))
 
+    def debug_stall(self, on: bool):
+        """Testing aid: make the reconstruction's bounded waits run out (see weno_solver_debug_stall)."""
+        capi.check(self._lib.weno_solver_debug_stall(self._h, 1 if on else 0))
+
     def check_instances(self, stream=None) -> np.ndarray:
         """Per-instance non-physical flags since the last check (cleared)."""
         out = np.zeros(self.n_instances, dtype=np.int32)

@@ -317,9 +317,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: far beyond any copy's latency
+// Waits for the barrier phase; gives up after kWaitLimitNs (or 2^26 polls) and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (int it = 1; it < (1 << 26); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -334,6 +345,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 #define WENO_K1_TILE 16  // cells per block tile of the TMA reconstruction (8, 16, 32 or 64)
 #endif
 static_assert(WENO_K1_TILE == 8 || WENO_K1_TILE == 16 || WENO_K1_TILE == 32 || WENO_K1_TILE == 64, "tile of 8, 16, 32 or 64 cells");
+
+#ifndef WENO_K1_GUNROLL
+#define WENO_K1_GUNROLL 1  // Gauss points per iteration of the reconstruction's Gauss loop
+#endif
+constexpr int kK1GaussUnroll = WENO_K1_GUNROLL;
 
 #ifndef WENO_K1_STAGES
 #define WENO_K1_STAGES 1  // shared-memory table buffers per block (2: prefetch the next tile while computing)
@@ -358,7 +374,7 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
     const __grid_constant__ CUtensorMap map_g1, const float* __restrict__ U, const float* __restrict__ Ulo,
     const int32_t* __restrict__ slot, const float4* __restrict__ gop4, const float* __restrict__ area, int64_t N,
     int64_t pitch, int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, int linear,
-    int* __restrict__ err) {
+    int* __restrict__ err, int stall) {
   using L = TmaTile<M, G>;
   constexpr int P = (M + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -366,8 +382,9 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
   const int tid = threadIdx.x;
   const int64_t ntiles = (N + L::TILE - 1) / L::TILE;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    // stall != 0 (testing aid): one arrival more than any thread makes, so the waits run out
+    mbar_init(&bar[0], stall ? 2 : 1);
+    mbar_init(&bar[1], stall ? 2 : 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
       const float2* sg1 = reinterpret_cast<const float2*>(base + L::GPM + L::DGS);
       const int cl = tid >> 2;
       float* out = Wg + (gbase + q * G) * 4 + v;
-#pragma unroll 1
+#pragma unroll kK1GaussUnroll
       for (int g = 0; g < G; ++g) {
         const float4 d = sds[g * L::TILE + cl];
         float2 gp[P], gn[P];

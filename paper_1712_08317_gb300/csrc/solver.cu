@@ -104,6 +104,7 @@ struct weno_solver_s {
   void *Wg = nullptr, *F = nullptr, *Ws = nullptr, *Wslo = nullptr;
   double *dt_dev = nullptr, *red = nullptr, *cell_dt = nullptr;
   int* flag = nullptr;
+  int debug_stall = 0;  // weno_solver_debug_stall
   std::vector<void*> allocs;
   Launch k1q, k1t, k2, k3q, k3t;
   cudaStream_t cap = nullptr;
@@ -155,11 +156,11 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
       if (s.nQ && (which & 1))
         weno::dev::k_reconstruct_tma<12, 8><<<tma_grid(s.k1q, s.nQ), TQ::THREADS, TQ::SMEM, st>>>(
             s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
-            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err);
+            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       if (s.nT && (which & 2))
         weno::dev::k_reconstruct_tma<9, 6><<<tma_grid(s.k1t, s.nT), TT::THREADS, TT::SMEM, st>>>(
             s.t_map_gpm, s.t_map_dgs, s.t_map_g1, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
-            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err);
+            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       return;
     }
   }
@@ -846,6 +847,14 @@ int weno_solver_launch_config(weno_solver_t s, int32_t* cfg) {
   cfg[0] = s->k1q.block; cfg[1] = s->k1q.grid;
   cfg[2] = s->k2.block;  cfg[3] = s->k2.grid;
   cfg[4] = s->k3q.block; cfg[5] = s->k3q.grid;
+  return WENO_OK;
+}
+
+int weno_solver_debug_stall(weno_solver_t s, int32_t on) {
+  if (!s) return fail(WENO_EINVAL, "null argument");
+  if (!s->tma) return fail(WENO_EINVAL, "this solver's kernels have no bounded waits (FP32C Euler only)");
+  s->debug_stall = on != 0;
+  s->drop_graphs();
   return WENO_OK;
 }
 

@@ -204,6 +204,27 @@ def test_nonphysical_flags_name_the_instance(precision):
     assert e.value.code == _capi.WENO_ENONPHYS and "1 of 3" in str(e.value)
 
 
+def test_bounded_wait_reports_timeout_and_context_survives():
+    mi, W, _ = _oracle("euler-mixed")
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c")
+    U, Ul = sol.to_device(W)
+    R0 = sol.residual(U, Ul).clone()
+    sol.check()
+    sol.debug_stall(True)          # barriers expect an arrival nobody makes: every wait runs out (1 s)
+    sol.residual(U, Ul)
+    with pytest.raises(_capi.WenoError) as e:
+        sol.check()
+    assert e.value.code == _capi.WENO_ETIMEOUT
+    sol.debug_stall(False)
+    R1 = sol.residual(U, Ul)
+    sol.check()
+    assert torch.equal(R0, R1)     # the context is still usable and the results are unchanged
+    sol64 = Solver(Mesh.from_input(mi), eqn="euler", precision="fp64")
+    with pytest.raises(_capi.WenoError) as e:
+        sol64.debug_stall(True)
+    assert e.value.code == _capi.WENO_EINVAL
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_autotune_does_not_change_results(precision):
     mi, W, _ = _oracle("euler-mixed")
