@@ -29,6 +29,11 @@ if ROOT not in sys.path:
 METRIC = "WENO3 cell-updates/s (×RK stages) on 1 GB300, FP32+batched vs FP64 at stated L1 error"
 UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
+FP32_LANES_PER_SM = 128        # Blackwell SM: 4 partitions x 32 FP32 lanes, one FMA per lane per clock
+# DRAM bytes per cell of one reconstruction launch (ncu dram__bytes_read.sum + dram__bytes_write.sum
+# of k_reconstruct_tma on the 637k-cell mesh of the same family, divided by its cells; the command is in
+# profiles/k_reconstruct_tma_n700_fp32c.md).  Set to None whenever that kernel changes until re-measured.
+K1_TRAFFIC_PER_CELL = {"quad": 1305.6, "tri": 851.1}
 WORKLOAD_N = 1754
 
 
@@ -214,6 +219,20 @@ def k1_bytes(nQ, nT, nv, esz, comp):
     def per(M, G):
         state = nv * esz * (2 if comp else 1)
         return state + 4 * M + 4 * M * esz + 2 * G * esz + G * M * esz + esz + G * nv * esz
+    return nQ * per(12, 8) + nT * per(9, 6)
+
+
+def k1_ops(nQ, nT, nv=4):
+    """Algorithmic FP32 operations (an FMA counts one) of one reconstruction pass (Sections 3.1-3.4).
+
+    Per (cell, variable): 3 per stencil slot (Delta W from hi and lo) and 8 per candidate
+    (gradient 4, beta 3, beta + eps 1); per Gauss point and candidate 16 (P^1_j(x_G) - W0: 2;
+    per sign: q = gamma beta, q + q^2, beta (1 + q + q^2) + eps, its square, alpha = gamma r,
+    sum alpha, sum alpha p: 7); per Gauss point 10 for R = W0 + sigma+ B+/A+ - sigma- B-/A-.
+    Reciprocals (2 per Gauss point and candidate, 2 per Gauss point) run on the MUFU pipe and are
+    not counted."""
+    def per(M, G):
+        return nv * (11 * M + G * (16 * M + 10))
     return nQ * per(12, 8) + nT * per(9, 6)
 
 
@@ -406,6 +425,12 @@ def main():
     peak, peak_kind = hbm_peak()
     kbytes = k1_bytes(nQ, nT, 4, 4, True)
     achieved = kbytes / (k_ms / 1e3) / 1e9
+    kops = k1_ops(nQ, nT)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (clk.get("sm_max_mhz") if isinstance(clk, dict) else None) or 2070.0
+    alu_peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    alu_achieved = kops / (k_ms / 1e3) / 1e12
+    traffic = (nQ * K1_TRAFFIC_PER_CELL["quad"] + nT * K1_TRAFFIC_PER_CELL["tri"]) if K1_TRAFFIC_PER_CELL else None
 
     # end to end through the public API with host state: H2D copy, step, D2H copy every step
     hostU = torch.empty(U.shape, dtype=U.dtype, pin_memory=True)
@@ -500,10 +525,17 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "steps": e2e_steps},
-            "roofline": {"kernel": "k_reconstruct (quad + triangle launches of one pass)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": f"{peak_kind} HBM copy bandwidth", "traffic": None,
-                         "algorithmic_bytes_per_launch": kbytes, "ms_per_launch": k_ms},
+            # the reconstruction is bound by FP32 arithmetic (FMA pipe and issue), not by HBM: see
+            # profiles/k_reconstruct_tma_n700_fp32c.md; the HBM view the design target names follows
+            "roofline": {"kernel": "k_reconstruct_tma (quad + triangle launches of one pass)", "bound": "alu",
+                         "achieved": alu_achieved, "peak": alu_peak, "unit": "Top/s (FP32 lane ops, FMA = 1)",
+                         "frac": alu_achieved / alu_peak,
+                         "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz",
+                         "traffic": traffic, "algorithmic_ops_per_launch": kops, "ms_per_launch": k_ms},
+            "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
+                             "algorithmic_bytes_per_launch": kbytes,
+                             "traffic_frac": (traffic / (k_ms / 1e3) / 1e9 / peak) if traffic else None},
             "kernel_ms": {"reconstruct": k_ms, "face": face_ms, "gather": gather_ms},
             "fp64": {"value": fp64_value, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64_ms / fp64_steps,
                      "fp32c_over_fp64": value / fp64_value},

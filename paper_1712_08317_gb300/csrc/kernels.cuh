@@ -194,7 +194,8 @@ __device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const fl
     }
     return sp * (ap.x + ap.y) - sm * (an.x + an.y);
   }
-  float2 Ap = f2(0.f, 0.f), Bp = f2(0.f, 0.f), Am = f2(0.f, 0.f), Bm = f2(0.f, 0.f);
+  // sums of alpha+- and alpha+- p: pair 0 initialises them, later pairs add
+  float2 Ap, Bp, Am, Bm;
 #pragma unroll
   for (int k = 0; k < P; ++k) {
     const float2 p = __ffma2_rn(c.gx[k], dx2, __fmul2_rn(c.gy[k], dy2));  // P^1_j(x_G) - W0
@@ -203,10 +204,13 @@ __device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const fl
     const float2 bn = __ffma2_rn(c.b[k], __ffma2_rn(qn, qn, qn), c.be[k]);
     const float2 ap = __fmul2_rn(gpos[k], rcp2(__fmul2_rn(bp, bp)));
     const float2 an = __fmul2_rn(gneg[k], rcp2(__fmul2_rn(bn, bn)));
-    Ap = __fadd2_rn(Ap, ap);
-    Bp = __ffma2_rn(ap, p, Bp);
-    Am = __fadd2_rn(Am, an);
-    Bm = __ffma2_rn(an, p, Bm);
+    if (k == 0) {
+      Ap = ap; Bp = __fmul2_rn(ap, p);
+      Am = an; Bm = __fmul2_rn(an, p);
+    } else {
+      Ap = __fadd2_rn(Ap, ap); Bp = __ffma2_rn(ap, p, Bp);
+      Am = __fadd2_rn(Am, an); Bm = __ffma2_rn(an, p, Bm);
+    }
   }
   return sp * (Bp.x + Bp.y) * rcp_approx(Ap.x + Ap.y) - sm * (Bm.x + Bm.y) * rcp_approx(Am.x + Am.y);
 }
@@ -346,11 +350,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 #endif
 static_assert(WENO_K1_TILE == 8 || WENO_K1_TILE == 16 || WENO_K1_TILE == 32 || WENO_K1_TILE == 64, "tile of 8, 16, 32 or 64 cells");
 
-#ifndef WENO_K1_GUNROLL
-#define WENO_K1_GUNROLL 1  // Gauss points per iteration of the reconstruction's Gauss loop
-#endif
-constexpr int kK1GaussUnroll = WENO_K1_GUNROLL;
-
 #ifndef WENO_K1_STAGES
 #define WENO_K1_STAGES 1  // shared-memory table buffers per block (2: prefetch the next tile while computing)
 #endif
@@ -432,7 +431,7 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
       const float2* sg1 = reinterpret_cast<const float2*>(base + L::GPM + L::DGS);
       const int cl = tid >> 2;
       float* out = Wg + (gbase + q * G) * 4 + v;
-#pragma unroll kK1GaussUnroll
+#pragma unroll 1
       for (int g = 0; g < G; ++g) {
         const float4 d = sds[g * L::TILE + cl];
         float2 gp[P], gn[P];
@@ -464,6 +463,30 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
 template <typename T>
 struct Prm { T gas_gamma, ax, ay; };
 
+#ifndef WENO_K2_FAST
+#define WENO_K2_FAST 1  // FP32 flux with approximate reciprocal / square root (FP64 always exact); 0: IEEE-rounded
+#endif
+
+// Division and square root of the flux: IEEE-rounded, or for FP32 with WENO_K2_FAST the
+// hardware approximations (rcp.approx / sqrt.approx, a few ulp), which FP32 rounding of the
+// Gauss values already dominates.
+template <typename T> struct FluxMath {
+  static __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+  static __device__ __forceinline__ T div(T a, T b) { return a / b; }
+  static __device__ __forceinline__ T sqr(T x) { return sqrt(x); }
+};
+#if WENO_K2_FAST
+template <> struct FluxMath<float> {
+  static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
+  static __device__ __forceinline__ float sqr(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+};
+#endif
+
 template <typename T>
 __device__ __forceinline__ void euler_x_flux(T r, T un, T ut, T E, T p, T f[4]) {
   f[0] = r * un;
@@ -476,37 +499,38 @@ __device__ __forceinline__ void euler_x_flux(T r, T un, T ut, T E, T p, T f[4]) 
 template <typename T>
 __device__ __forceinline__ void hllc(const T wl[4], const T wr[4], T nx, T ny, T gam, T out[4], bool& bad) {
   const T rl = wl[0], rr = wr[0];
-  const T irl = T(1) / rl, irr = T(1) / rr;
+  using FM = FluxMath<T>;
+  const T irl = FM::rcp(rl), irr = FM::rcp(rr);
   const T ul = (wl[1] * nx + wl[2] * ny) * irl, vl = (wl[2] * nx - wl[1] * ny) * irl;
   const T ur = (wr[1] * nx + wr[2] * ny) * irr, vr = (wr[2] * nx - wr[1] * ny) * irr;
   const T pl = (gam - T(1)) * (wl[3] - T(0.5) * rl * (ul * ul + vl * vl));
   const T pr = (gam - T(1)) * (wr[3] - T(0.5) * rr * (ur * ur + vr * vr));
   bad |= !(rl > T(0)) || !(rr > T(0)) || !(pl > T(0)) || !(pr > T(0)) || !(wl[3] == wl[3]) || !(wr[3] == wr[3]);
-  const T cl = sqrt(gam * pl * irl), cr = sqrt(gam * pr * irr);
+  const T cl = FM::sqr(gam * pl * irl), cr = FM::sqr(gam * pr * irr);
   // Roe averages
-  const T sl = sqrt(rl), sr = sqrt(rr), iw = T(1) / (sl + sr);
+  const T sl = FM::sqr(rl), sr = FM::sqr(rr), iw = FM::rcp(sl + sr);
   const T ua = (sl * ul + sr * ur) * iw, va = (sl * vl + sr * vr) * iw;
   const T Hl = (wl[3] + pl) * irl, Hr = (wr[3] + pr) * irr;
   const T Ha = (sl * Hl + sr * Hr) * iw;
-  const T ca = sqrt((gam - T(1)) * (Ha - T(0.5) * (ua * ua + va * va)));
+  const T ca = FM::sqr((gam - T(1)) * (Ha - T(0.5) * (ua * ua + va * va)));
   const T SL = fmin(ul - cl, ua - ca), SR = fmax(ur + cr, ua + ca);
   const T ml = rl * (SL - ul), mr = rr * (SR - ur);
-  const T SS = (pr - pl + ul * ml - ur * mr) / (ml - mr);
+  const T SS = FM::div(pr - pl + ul * ml - ur * mr, ml - mr);
   T f[4];
   if (SL >= T(0)) {
     euler_x_flux(rl, ul, vl, wl[3], pl, f);
   } else if (SS >= T(0)) {
     euler_x_flux(rl, ul, vl, wl[3], pl, f);
-    const T k = ml / (SL - SS);  // rho* of the left star state
-    const T Es = k * (wl[3] * irl + (SS - ul) * (SS + pl / ml));
+    const T k = FM::div(ml, SL - SS);  // rho* of the left star state
+    const T Es = k * (wl[3] * irl + (SS - ul) * (SS + FM::div(pl, ml)));
     f[0] += SL * (k - rl);
     f[1] += SL * (k * SS - rl * ul);
     f[2] += SL * (k * vl - rl * vl);
     f[3] += SL * (Es - wl[3]);
   } else if (SR > T(0)) {
     euler_x_flux(rr, ur, vr, wr[3], pr, f);
-    const T k = mr / (SR - SS);
-    const T Es = k * (wr[3] * irr + (SS - ur) * (SS + pr / mr));
+    const T k = FM::div(mr, SR - SS);
+    const T Es = k * (wr[3] * irr + (SS - ur) * (SS + FM::div(pr, mr)));
     f[0] += SR * (k - rr);
     f[1] += SR * (k * SS - rr * ur);
     f[2] += SR * (k * vr - rr * vr);
