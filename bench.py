@@ -120,17 +120,37 @@ def oracle_sample(seconds=10.0, n=60, steps=None):
                       f"({mi.n_cells} cells), {el:.1f} s, single-threaded elementwise numpy"}, mi.n_cells, el, done
 
 
-def dist_setup():
+def dist_setup(backend=None):
+    """One process per GPU under torchrun (RANK / LOCAL_RANK / WORLD_SIZE / MASTER_* from the env).
+    Every rank runs its own replica of the workload (the path has no exchange step); the process
+    group only carries barriers and the max-over-ranks timing."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
         return dist, rank, ws
     return None, 0, 1
+
+
+def max_over_ranks(dist, value, device="cpu"):
+    """The slowest rank's time (whole-job rates divide the work of all ranks by it)."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, cells, stages, ms):
+    """cell-updates/s of ws replicas of `cells` cells through `stages` RK stages in ms milliseconds."""
+    return ws * cells * stages / (ms / 1e3)
 
 
 def run_reference(args):
@@ -163,7 +183,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, torch, stream):
+def run_batched(args, torch, stream, dist=None, ws=1):
     """256 independent instances (cells log-uniform in [5k, 200k]; quad / tri / mixed; smooth or
     Riemann data) in one flattened launch per kernel, one dt per instance."""
     import synthetic as S
@@ -195,16 +215,18 @@ def run_batched(args, torch, stream):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     steps = args.batch_steps
+    if dist:
+        dist.barrier()
     e0.record(stream)
     for _ in range(steps):
         sol.step_instances(U, Ul, dt_dev)
     e1.record(stream)
     torch.cuda.synchronize()
     bad = np.maximum(bad_warm, sol.check_instances())
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(dist, e0.elapsed_time(e1), torch.device("cuda", torch.cuda.current_device()))
     n = sol.n_cells
     info = big.info
-    return {"value": n * 3 * steps / (ms / 1e3), "unit": UNIT, "instances": len(descs), "cells": n,
+    return {"value": whole_job_rate(ws, n, 3 * steps, ms), "unit": UNIT, "instances": len(descs), "cells": n,
             "quads": int(info.n_quads), "triangles": int(info.n_tris), "steps": steps,
             "ms_per_step": ms / steps, "setup_s": round(setup, 1), "precision": "fp32c",
             "dt_range": [float(dts.min()), float(dts.max())],
@@ -311,7 +333,7 @@ def run_accuracy(args):
     print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "eps": args.eps}), flush=True)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -331,7 +353,11 @@ def main():
     ap.add_argument("--cfl", type=float, default=0.5, help="CFL number of the accuracy runs")
     ap.add_argument("--precisions", default="fp64,fp32c")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
-    args = ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def main():
+    args = parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
@@ -385,15 +411,11 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
     sol.check()
     c_end = sol.conservation(U, Ul)[0]
     steps_done = args.warmup + args.steps
-    value = ws * N * 3 * args.steps / (ms / 1e3)
+    value = whole_job_rate(ws, N, 3 * args.steps, ms)
 
     # dominant kernel alone: the reconstruction pass, timed with events on its stream
     reps = 20
@@ -441,6 +463,8 @@ def main():
     torch.cuda.synchronize()
     x0 = torch.cuda.Event(enable_timing=True)
     x1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
     x0.record(stream)
     for _ in range(e2e_steps):
         U.copy_(hostU, non_blocking=True)
@@ -450,9 +474,9 @@ def main():
         hostUl.copy_(Ul, non_blocking=True)
     x1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = x0.elapsed_time(x1)
+    e2e_ms = max_over_ranks(dist, x0.elapsed_time(x1), dev)
     steps_done += e2e_steps
-    e2e_value = ws * N * 3 * e2e_steps / (e2e_ms / 1e3)
+    e2e_value = whole_job_rate(ws, N, 3 * e2e_steps, e2e_ms)
     nbytes = U.numel() * 4 * 2
 
     # FP64 path on the same mesh (tables reused from the mesh's FP64 precompute)
@@ -469,13 +493,15 @@ def main():
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
     f0.record(stream)
     for _ in range(fp64_steps):
         sol64.step(V, None, dt)
     f1.record(stream)
     torch.cuda.synchronize()
-    fp64_ms = f0.elapsed_time(f1)
-    fp64_value = ws * N * 3 * fp64_steps / (fp64_ms / 1e3)
+    fp64_ms = max_over_ranks(dist, f0.elapsed_time(f1), dev)
+    fp64_value = whole_job_rate(ws, N, 3 * fp64_steps, fp64_ms)
     sol64.check()
 
     # accuracy at t = (steps done) dt: FP32C vs FP64 vs the exact translated vortex
@@ -510,7 +536,7 @@ def main():
     if args.batch > 0:
         del sol, U, Ul, hostU, hostUl
         torch.cuda.empty_cache()
-        batched = run_batched(args, torch, stream)
+        batched = run_batched(args, torch, stream, dist, ws)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
