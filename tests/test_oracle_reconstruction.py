@@ -128,3 +128,38 @@ def test_optimisation_brings_large_weights_to_order_one():
     assert raw > 10.0
     assert opt <= golden.max() * 1.5
     assert opt < raw / 5
+
+
+@pytest.mark.parametrize("cfg,kind", [(2, "quad"), (2, "tri"), (2, "mixed"), (3, "mixed"), (5, None)])
+def test_rank_of_B_is_members_minus_two(cfg, kind):
+    """Section 3.1: with all 13 stencil cells distinct the 13 x 12 system has rank 11, two equations
+    being implied by linear exactness; in general rank(B) = (distinct members incl. i0) - 2, so a
+    triangle with 10 members gives 8 and a quad with i9..i12 missing (valence-4 nodes) gives 7."""
+    from oracle.mesh import SLOT_MISSING
+    mi = S.mesh_for_config(cfg, n=10, seed=5, kind=kind) if cfg != 5 else S.stretched_vortex_mesh(12, seed=5)
+    mesh = OracleMesh.from_input(mi)
+    seen = set()
+    for t in precompute(mesh, Params()):
+        for n in range(len(t.cells)):
+            members = 1 + sum(1 for s in mesh.slots[t.cells[n]][1:] if s[0] != SLOT_MISSING)
+            for g in range(t.G):
+                B = t.B[n, g]
+                assert np.linalg.matrix_rank(B, tol=1e-10 * np.abs(B).max()) == members - 2
+            seen.add((t.M, members))
+    assert seen  # (M, members) pairs met: one for uniform-valence meshes, several for mixed ones
+
+
+def test_zeta_regularised_solves_converge_to_the_minimum_norm_solution(outflow_case):
+    """Reading of Eqs. 12 and 15: the solution of (zeta I + M^T M) x = M^T r differs from the
+    zeta -> 0 limit, the minimum-norm least-squares solution, by O(zeta) (the remark after
+    Eq. 12), for the full-rank A and for the rank-deficient B alike."""
+    mi, mesh, groups = outflow_case
+    t = groups[0]
+    rng = np.random.default_rng(1)
+    for n in rng.choice(len(t.cells), 5, replace=False):
+        for M, r in ((t.A[n], rng.normal(size=t.A.shape[1])), (t.B[n, 0], t.eta[n, 0])):
+            x0 = np.linalg.pinv(M, rcond=1e-12) @ r
+            d = [np.abs(np.linalg.solve(z * np.eye(M.shape[1]) + M.T @ M, M.T @ r) - x0).max()
+                 for z in (1e-5, 1e-6, 1e-7)]
+            assert d[2] < d[1] < d[0] < 1e-2
+            assert 5.0 < d[0] / d[1] < 20.0 and 5.0 < d[1] / d[2] < 20.0   # linear in zeta
