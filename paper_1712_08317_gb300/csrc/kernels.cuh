@@ -463,10 +463,6 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
 template <typename T>
 struct Prm { T gas_gamma, ax, ay; };
 
-#ifndef WENO_K2_SPLIT
-#define WENO_K2_SPLIT 0  // 1: one thread per (face, Gauss point) instead of one per face
-#endif
-
 #ifndef WENO_K2_FAST
 #define WENO_K2_FAST 1  // FP32 flux with approximate reciprocal / square root (FP64 always exact); 0: IEEE-rounded
 #endif
@@ -618,66 +614,6 @@ __global__ void __launch_bounds__(256) k_face(
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] *= T(0.5) * len;
     store_vec<T, NV>(F + f * NV, acc);
-    if (bad) {  // every writer stores the same value
-      const int64_t cl = il < 8 * nQ ? il / 8 : nQ + (il - 8 * nQ) / 6;
-      flag[inst ? __ldg(inst + cl) : 0] = 1;
-    }
-  }
-}
-
-// Same flux with one thread per (face, Gauss point): twice the threads (more
-// loads in flight), the pair's two point fluxes combined with a lane shuffle in
-// the same order as k_face (F_0 + F_1), so the results are identical.
-template <typename T, int NV>
-__global__ void __launch_bounds__(256) k_face_split(
-    const T* __restrict__ Wg, const int32_t* __restrict__ gl, const int32_t* __restrict__ gr,
-    const T* __restrict__ fnx, const T* __restrict__ fny, const T* __restrict__ flen, int64_t nF,
-    T* __restrict__ F, Prm<T> prm, int* __restrict__ flag, const int32_t* __restrict__ inst, int64_t nQ) {
-  const int64_t total = 2 * nF;
-  const int lane = threadIdx.x & 31;
-  // warp-uniform loop: every lane of a warp reaches the shuffles
-  for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < total;
-       t0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = t0 + lane;
-    const bool act = t < total;
-    const int64_t f = act ? (t >> 1) : 0;
-    const int k = (int)(t & 1);
-    bool bad = false;
-    T fk[NV];
-    int64_t il = 0;
-    T len = T(0);
-    if (act) {
-      il = __ldg(gl + f);
-      const int64_t ir = __ldg(gr + f);
-      const T nx = __ldg(fnx + f), ny = __ldg(fny + f);
-      len = __ldg(flen + f);
-      T wl[NV], wr[NV];
-      load_vec<T, NV>(Wg + (il + k) * NV, wl);
-      // the right cell meets the left cell's point k at its point 1 - k
-      if (ir >= 0) load_vec<T, NV>(Wg + (ir + 1 - k) * NV, wr);
-      else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) wr[v] = wl[v];
-      }
-      if (NV == 4) {
-        hllc<T>(wl, wr, nx, ny, prm.gas_gamma, fk, bad);
-      } else {
-        const T an = prm.ax * nx + prm.ay * ny;
-        fk[0] = an * (an >= T(0) ? wl[0] : wr[0]);
-        bad |= !(fk[0] == fk[0]);
-      }
-    } else {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) fk[v] = T(0);
-    }
-    T acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T o = __shfl_xor_sync(0xffffffffu, fk[v], 1);
-      acc[v] = k == 0 ? fk[v] + o : o + fk[v];  // F_0 + F_1 on both lanes
-      acc[v] *= T(0.5) * len;
-    }
-    if (act && k == 0) store_vec<T, NV>(F + f * NV, acc);
     if (bad) {  // every writer stores the same value
       const int64_t cl = il < 8 * nQ ? il / 8 : nQ + (il - 8 * nQ) / 6;
       flag[inst ? __ldg(inst + cl) : 0] = 1;

@@ -194,16 +194,10 @@ void launch_reconstruct(S& s, const void* U, const void* Ulo, cudaStream_t st, i
 template <typename T, int NV, bool COMP>
 void launch_face(S& s, cudaStream_t st) {
   weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
-  if (s.nF) {
-    if (WENO_K2_SPLIT)
-      weno::dev::k_face_split<T, NV><<<grid_of(s.k2, 2 * s.nF), s.k2.block, 0, st>>>(
-          (const T*)s.Wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)s.F, p, s.flag,
-          s.inst, s.nQ);
-    else
-      weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
-          (const T*)s.Wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)s.F, p, s.flag,
-          s.inst, s.nQ);
-  }
+  if (s.nF)
+    weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
+        (const T*)s.Wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)s.F, p, s.flag,
+        s.inst, s.nQ);
 }
 
 template <typename T, int NV, bool COMP, int MODE>
