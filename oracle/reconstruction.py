@@ -56,6 +56,7 @@ class Params:
     eqn: str = "euler"       # "euler" or "scalar"
     gas_gamma: float = 1.4
     adv: tuple = (1.0, 1.0)  # advection velocity of the scalar equation
+    characteristic: bool = False  # Euler: reconstruct characteristic variables (Section 4)
 
 
 @dataclass

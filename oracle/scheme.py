@@ -48,7 +48,7 @@ class OracleSolver:
     def gauss_values(self, W: np.ndarray) -> np.ndarray:
         Wg = np.full((self.nv, self.mesh.n_cells, 8), np.nan)
         for t in self.groups:
-            Wg[:, t.cells, :t.G] = gauss_values_group(t, W, self.params)
+            Wg[:, t.cells, :t.G] = gauss_values_group(t, W, self.params, self.mesh)
         return Wg
 
     def face_fluxes(self, W: np.ndarray) -> np.ndarray:

@@ -1,0 +1,104 @@
+"""Oracle characteristic-variable reconstruction (Euler, Section 4) pinned by the eigen-structure
+of the flux Jacobian (complex-step derivative of the physical flux, independent of the formulas
+for R) and by identities of the projection."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import OracleMesh, OracleSolver, Params, precompute
+from oracle.flux import euler_normal_flux, pressure
+from oracle.weno import gauss_values_group, roe_eigenvectors
+
+GAMMA = 1.4
+
+
+def _prim(rho, u, v, p):
+    return np.array([rho, rho * u, rho * v, p / (GAMMA - 1) + 0.5 * rho * (u * u + v * v)])
+
+
+def _roe_state(Wl, Wr):
+    """Conservative state with the Roe averages u~, v~, H~ (and rho~ = sqrt(rho_l rho_r))."""
+    sl, sr = np.sqrt(Wl[0]), np.sqrt(Wr[0])
+    hl = (Wl[3] + pressure(Wl, GAMMA)) / Wl[0]
+    hr = (Wr[3] + pressure(Wr, GAMMA)) / Wr[0]
+    u = (sl * Wl[1] / Wl[0] + sr * Wr[1] / Wr[0]) / (sl + sr)
+    v = (sl * Wl[2] / Wl[0] + sr * Wr[2] / Wr[0]) / (sl + sr)
+    H = (sl * hl + sr * hr) / (sl + sr)
+    rho = sl * sr
+    p = (GAMMA - 1) / GAMMA * rho * (H - 0.5 * (u * u + v * v))
+    return _prim(rho, u, v, p), u, v, np.sqrt((GAMMA - 1) * (H - 0.5 * (u * u + v * v)))
+
+
+def _jacobian(W, nx, ny):
+    """d(F n_x + G n_y)/dW by the complex step (exact to rounding)."""
+    h = 1e-30
+    J = np.empty((4, 4))
+    for k in range(4):
+        Wc = W.astype(complex)
+        Wc[k] += 1j * h
+        J[:, k] = euler_normal_flux(Wc, nx, ny, GAMMA).imag / h
+    return J
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_eigenvectors_diagonalise_the_roe_jacobian(seed):
+    rng = np.random.default_rng(seed)
+    Wl = _prim(rng.uniform(0.1, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.05, 2))
+    Wr = Wl if seed == 0 else _prim(rng.uniform(0.1, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.05, 2))
+    th = rng.uniform(0, 2 * np.pi)
+    nx, ny = np.cos(th), np.sin(th)
+    R = roe_eigenvectors(Wl, Wr, nx, ny, GAMMA)
+    Wroe, u, v, a = _roe_state(Wl, Wr)
+    J = _jacobian(Wroe, nx, ny)
+    D = np.linalg.inv(R) @ J @ R
+    qn = u * nx + v * ny
+    lam = np.array([qn - a, qn, qn, qn + a])
+    scale = np.abs(lam).max()
+    assert np.abs(D - np.diag(lam)).max() < 1e-11 * scale
+
+
+@pytest.fixture(scope="module")
+def outflow_mixed():
+    mi = S.mesh_for_config(3, n=8, seed=2, kind="mixed")
+    mesh = OracleMesh.from_input(mi)
+    return mi, mesh, precompute(mesh, Params())
+
+
+def test_linear_scheme_is_unchanged_by_the_projection(outflow_mixed):
+    """Linear weights do not depend on the field, so R (sum gamma P^1(R^-1 W)) = sum gamma P^1(W)."""
+    mi, mesh, groups = outflow_mixed
+    W = S.four_quadrant_average(mi, seed=2)
+    for t in groups:
+        a = gauss_values_group(t, W, Params(linear=True), mesh)
+        b = gauss_values_group(t, W, Params(linear=True, characteristic=True), mesh)
+        assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+def test_constant_and_linear_states_are_reproduced(outflow_mixed):
+    mi, mesh, groups = outflow_mixed
+    W = np.stack([np.full(mesh.n_cells, x) for x in _prim(0.9, 0.3, -0.2, 1.1)])
+    lin = S.cell_average(mi, lambda x, y: np.stack([1 + 0.1 * x, 0.2 + 0.05 * y, -0.1 + 0.02 * x, 2.5 + 0.1 * y]),
+                         order=3)
+    prm = Params(characteristic=True)
+    for t in groups:
+        assert np.abs(gauss_values_group(t, W, prm, mesh) - W[:, t.cells, None]).max() < 1e-13
+        # linear data: interior cells (no mirror images in the stencil) reproduce it at the Gauss points
+        from oracle.mesh import SLOT_GHOST
+        inner = np.array([all(s[0] != SLOT_GHOST for s in mesh.slots[c]) for c in t.cells])
+        xG = mesh.cell_gauss[t.cells, :t.G]
+        exact = np.stack([1 + 0.1 * xG[..., 0], 0.2 + 0.05 * xG[..., 1], -0.1 + 0.02 * xG[..., 0],
+                          2.5 + 0.1 * xG[..., 1]])
+        got = gauss_values_group(t, lin, prm, mesh)
+        assert inner.sum() > 3
+        assert np.abs(got - exact)[:, inner].max() < 1e-10
+
+
+def test_characteristic_residual_conserves_and_differs_from_componentwise():
+    mi = S.mesh_for_config(2, n=8, seed=3, kind="mixed")
+    W = S.cell_average(mi, S.density_wave, order=3)
+    W[0] += 0.3 * (S.cell_average(mi, lambda x, y: (np.abs(x - 1) < 0.4)[None] * 1.0, order=3)[0])
+    mesh = OracleMesh.from_input(mi)
+    rc = OracleSolver(mesh, Params(characteristic=True)).residual(W)
+    r0 = OracleSolver(mesh, Params()).residual(W)
+    assert np.abs((rc * mesh.area).sum(axis=1)).max() < 1e-12 * np.abs(rc * mesh.area).max()
+    assert np.abs(rc - r0).max() > 1e-6 * np.abs(r0).max()
