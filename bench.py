@@ -33,7 +33,7 @@ FP32_LANES_PER_SM = 128        # Blackwell SM: 4 partitions x 32 FP32 lanes, one
 # DRAM bytes per cell of one reconstruction launch (ncu dram__bytes_read.sum + dram__bytes_write.sum
 # of k_reconstruct_tma on the 637k-cell mesh of the same family, divided by its cells; the command is in
 # profiles/k_reconstruct_tma_n700_fp32c.md).  Set to None whenever that kernel changes until re-measured.
-K1_TRAFFIC_PER_CELL = None
+K1_TRAFFIC_PER_CELL = {"quad": 1305.7, "tri": 850.3}
 WORKLOAD_N = 1754
 
 
