@@ -345,6 +345,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched leg (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--char-steps", type=int, default=20, help="steps of the characteristic-variable leg (0: skip)")
     ap.add_argument("--accuracy", action="store_true", help="convergence ladders to t = 2 instead of the timing run")
     ap.add_argument("--acc-n", type=int, default=160, help="density-wave mesh of the t = 2 accuracy block (0: skip)")
     ap.add_argument("--ladder-dw", default="20,40,80,160,320")
@@ -523,6 +524,33 @@ def main():
                "l1_rho_fp64_vs_exact": l1(W64 - ex), "l1_rho_fp32c_vs_fp64": l1(W32 - W64),
                "conservation_rel_drift_fp32c": float(np.abs(c_end - c_start).max() / np.abs(c_start).max())}
 
+    # characteristic-variable reconstruction (Section 4) on the same mesh, FP32C
+    char = None
+    if args.char_steps > 0:
+        solc = Solver(mesh, eqn="euler", precision="fp32c", characteristic=True)
+        Uc, Ulc = solc.to_device(W0)
+        if not args.no_autotune:
+            solc.autotune(Uc, Ulc)
+        for _ in range(3):
+            solc.step(Uc, Ulc, dt)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(args.char_steps):
+            solc.step(Uc, Ulc, dt)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        char_ms = max_over_ranks(dist, h0.elapsed_time(h1), dev)
+        solc.check()
+        char = {"value": whole_job_rate(ws, N, 3 * args.char_steps, char_ms), "unit": UNIT,
+                "steps": args.char_steps, "ms_per_step": char_ms / args.char_steps, "precision": "fp32c",
+                "reconstruction": "characteristic variables (Roe-averaged normal Jacobian per face)"}
+        del solc, Uc, Ulc
+        torch.cuda.empty_cache()
+
     # accuracy to t = 2 on the density-wave mesh of 51,200 split triangles (FP64 vs FP32C vs exact)
     acc_t2 = None
     if rank == 0 and args.acc_n > 0:
@@ -566,6 +594,7 @@ def main():
             "fp64": {"value": fp64_value, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64_ms / fp64_steps,
                      "fp32c_over_fp64": value / fp64_value},
             "batched": batched,
+            "characteristic": char,
             "accuracy": acc,
             "accuracy_t2": acc_t2,
             "cpu_baseline": cpu,

@@ -83,6 +83,9 @@ typedef struct {
   int32_t optimize;   /* 1: optimised linear weights of Section 3.3 (default), 0: raw      */
   int32_t linear;     /* 1: linear scheme R = sum gamma_j P^1_j (Eq. 14), 0: WENO          */
   int32_t n_threads;  /* host threads for the precompute (0 = all hardware threads)        */
+  int32_t characteristic; /* Euler: 1 = reconstruct characteristic variables per face (Section 4:
+                         normal flux Jacobian at the Roe average of the two cells), 0 =
+                         component-wise (default)                                          */
 } weno_params;
 
 typedef struct {
@@ -96,7 +99,7 @@ typedef struct {
 } weno_mesh_info;
 
 /* Fills *p with the defaults: Euler, FP64, gamma 1.4, adv (1,1), eps 1e-6,
- * theta 3, rcond 1e-12, optimize 1, linear 0, n_threads 0. */
+ * theta 3, rcond 1e-12, optimize 1, linear 0, n_threads 0, characteristic 0. */
 void weno_params_default(weno_params* p);
 
 /* Builds a mesh (Section 2; stencils of Sections 3.1 and 3.2).

@@ -23,7 +23,7 @@ class weno_mesh_opts(C.Structure):
 class weno_params(C.Structure):
     _fields_ = [("eqn", C.c_int32), ("precision", C.c_int32), ("gas_gamma", C.c_double), ("adv", C.c_double * 2),
                 ("eps", C.c_double), ("theta", C.c_double), ("rcond", C.c_double), ("optimize", C.c_int32),
-                ("linear", C.c_int32), ("n_threads", C.c_int32)]
+                ("linear", C.c_int32), ("n_threads", C.c_int32), ("characteristic", C.c_int32)]
 
 
 class weno_mesh_info(C.Structure):

@@ -93,7 +93,7 @@ class Mesh:
 
 
 def params_struct(eqn="euler", precision="fp64", gas_gamma=1.4, adv=(1.0, 1.0), eps=1e-6, theta=3.0,
-                  rcond=1e-12, optimize=True, linear=False, n_threads=0):
+                  rcond=1e-12, optimize=True, linear=False, n_threads=0, characteristic=False):
     p = capi.weno_params()
     capi.load().weno_params_default(C.byref(p))
     p.eqn = capi.WENO_EQN_EULER if eqn == "euler" else capi.WENO_EQN_SCALAR
@@ -106,6 +106,7 @@ def params_struct(eqn="euler", precision="fp64", gas_gamma=1.4, adv=(1.0, 1.0), 
     p.optimize = int(bool(optimize))
     p.linear = int(bool(linear))
     p.n_threads = n_threads
+    p.characteristic = int(bool(characteristic))
     return p
 
 

@@ -621,6 +621,153 @@ __global__ void __launch_bounds__(256) k_face(
   }
 }
 
+// ---------------------------------------------------------------- K1, characteristic variables
+// Euler (Section 4): the Gauss points of local face k are reconstructed in the
+// characteristic variables of the normal flux Jacobian at the Roe average of
+// the cell and its neighbour across face k (stencil slot k+1; the cell itself
+// at an outflow boundary).  Four consecutive lanes hold one cell; lane l
+// gathers variable l of the stencil, projects the stencil differences onto
+// field l with row l of R^-1 (lane shuffles bring the other variables),
+// reconstructs field l, and returns variable l of W0 + R dU with row l of R.
+// Reconstructing the increment dU (zero for constant data) keeps constant
+// states exact whatever the rounding of R R^-1.
+template <typename T> __device__ __forceinline__ T rcp_exact(T x) { return T(1) / x; }
+
+template <typename T>
+__device__ __forceinline__ T lane_sum4(const T c[4], T x, int base) {
+  T r = T(0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r += c[i] * __shfl_sync(0xffffffffu, x, base + i);
+  return r;
+}
+
+template <typename T, int M, int G, bool COMP>
+__global__ void __launch_bounds__(256) k_reconstruct_char(
+    const T* __restrict__ U, const T* __restrict__ Ulo, const int32_t* __restrict__ slot,
+    const T* __restrict__ gop, const T* __restrict__ dg, const T* __restrict__ gam,
+    const T* __restrict__ area, int64_t N, int64_t first, int64_t gbase, T* __restrict__ Wg,
+    T eps, T theta, T gas_gamma, int linear) {
+  const int lane = threadIdx.x & 31, base = lane & ~3, l = lane & 3;
+  const int64_t total = N * 4;
+  // warp-uniform loop: every lane reaches the shuffles; lanes past the end work on cell 0
+  for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < total;
+       t0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = t0 + lane;
+    const bool act = t < total;
+    const int64_t q = act ? (t >> 2) : 0;
+    const int64_t c = first + q;
+    T W0[4];
+    load_vec<T, 4>(U + c * 4, W0);
+    const T w0 = W0[l];
+    const T l0 = COMP ? __ldg(Ulo + c * 4 + l) : T(0);
+    T dW[M + 1];
+    dW[0] = T(0);
+#pragma unroll
+    for (int s = 1; s <= M; ++s) {
+      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
+      T d = __ldg(U + cs * 4 + l) - w0;
+      if (COMP) d += __ldg(Ulo + cs * 4 + l) - l0;
+      dW[s] = d;
+    }
+    const T a0 = __ldg(area + c);
+    const T gm1 = gas_gamma - T(1);
+    const T rl = W0[0], ul = W0[1] / rl, vl = W0[2] / rl;
+    const T hl = (W0[3] + gm1 * (W0[3] - T(0.5) * rl * (ul * ul + vl * vl))) / rl;
+    const T sl = sqrt(rl);
+#pragma unroll 1
+    for (int k = 0; k < G / 2; ++k) {
+      // face frame: Roe average with the neighbour, outward normal from the face's two Gauss points
+      T Wn[4];
+      load_vec<T, 4>(U + (int64_t)__ldg(slot + (int64_t)k * N + q) * 4, Wn);  // slot k+1: across face k
+      const T rr = Wn[0], ur = Wn[1] / rr, vr = Wn[2] / rr;
+      const T hr = (Wn[3] + gm1 * (Wn[3] - T(0.5) * rr * (ur * ur + vr * vr))) / rr;
+      const T sr = sqrt(rr), iw = T(1) / (sl + sr);
+      const T u = (sl * ul + sr * ur) * iw, v = (sl * vl + sr * vr) * iw, H = (sl * hl + sr * hr) * iw;
+      const T kin = T(0.5) * (u * u + v * v);
+      const T a = sqrt(gm1 * (H - kin)), ia = T(1) / a;
+      const T x0 = __ldg(dg + (int64_t)(4 * k) * N + q), y0 = __ldg(dg + (int64_t)(4 * k + 1) * N + q);
+      const T x1 = __ldg(dg + (int64_t)(4 * k + 2) * N + q), y1 = __ldg(dg + (int64_t)(4 * k + 3) * N + q);
+      const T tx = x1 - x0, ty = y1 - y0, it = T(1) / sqrt(tx * tx + ty * ty);
+      const T nx = ty * it, ny = -tx * it;
+      const T qn = u * nx + v * ny, qt = v * nx - u * ny;
+      const T b1 = gm1 * ia * ia, b2 = b1 * kin;
+      // row l of R^-1 (fields: q_n - a, entropy, shear, q_n + a) and row l of R
+      T Lr[4], Rr[4];
+      if (l == 0) {
+        Lr[0] = T(0.5) * (b2 + qn * ia); Lr[1] = T(-0.5) * (b1 * u + nx * ia);
+        Lr[2] = T(-0.5) * (b1 * v + ny * ia); Lr[3] = T(0.5) * b1;
+        Rr[0] = T(1); Rr[1] = T(1); Rr[2] = T(0); Rr[3] = T(1);
+      } else if (l == 1) {
+        Lr[0] = T(1) - b2; Lr[1] = b1 * u; Lr[2] = b1 * v; Lr[3] = -b1;
+        Rr[0] = u - a * nx; Rr[1] = u; Rr[2] = -ny; Rr[3] = u + a * nx;
+      } else if (l == 2) {
+        Lr[0] = -qt; Lr[1] = -ny; Lr[2] = nx; Lr[3] = T(0);
+        Rr[0] = v - a * ny; Rr[1] = v; Rr[2] = nx; Rr[3] = v + a * ny;
+      } else {
+        Lr[0] = T(0.5) * (b2 - qn * ia); Lr[1] = T(0.5) * (nx * ia - b1 * u);
+        Lr[2] = T(0.5) * (ny * ia - b1 * v); Lr[3] = T(0.5) * b1;
+        Rr[0] = H - a * qn; Rr[1] = kin; Rr[2] = qt; Rr[3] = H + a * qn;
+      }
+      // project the stencil differences onto field l, then candidate gradients and indicators
+      T dU[M + 1];
+      dU[0] = T(0);
+#pragma unroll
+      for (int s = 1; s <= M; ++s) dU[s] = lane_sum4(Lr, dW[s], base);
+      T gx[M], gy[M], beta[M];
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        const T da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
+        const T m0 = __ldg(gop + (int64_t)(j * 4 + 0) * N + q), m1 = __ldg(gop + (int64_t)(j * 4 + 1) * N + q);
+        const T m2 = __ldg(gop + (int64_t)(j * 4 + 2) * N + q), m3 = __ldg(gop + (int64_t)(j * 4 + 3) * N + q);
+        gx[j] = m0 * da + m1 * db;
+        gy[j] = m2 * da + m3 * db;
+        beta[j] = a0 * (gx[j] * gx[j] + gy[j] * gy[j]);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int g = 2 * k + h;
+        const T dx = __ldg(dg + (int64_t)(g * 2) * N + q), dy = __ldg(dg + (int64_t)(g * 2 + 1) * N + q);
+        const T* gg = gam + (int64_t)(g * M) * N + q;
+        T incr;
+        if (linear) {
+          incr = T(0);
+#pragma unroll
+          for (int j = 0; j < M; ++j) incr += __ldg(gg + (int64_t)j * N) * (gx[j] * dx + gy[j] * dy);
+        } else {
+          T sp = T(0), sm = T(0);
+#pragma unroll
+          for (int j = 0; j < M; ++j) {
+            const T gj = __ldg(gg + (int64_t)j * N);
+            const T tp = T(0.5) * (gj + theta * fabs_(gj));
+            sp += tp;
+            sm += tp - gj;
+          }
+          const T isp = T(1) / sp, ism = T(1) / sm;
+          T Ap = T(0), Bp = T(0), Am = T(0), Bm = T(0);
+#pragma unroll
+          for (int j = 0; j < M; ++j) {
+            const T gj = __ldg(gg + (int64_t)j * N);
+            const T tp = T(0.5) * (gj + theta * fabs_(gj));
+            const T gp = tp * isp, gmn = (tp - gj) * ism;
+            const T p = gx[j] * dx + gy[j] * dy;
+            const T qp = gp * beta[j], qm = gmn * beta[j];
+            const T bp = beta[j] * (T(1) + qp + qp * qp) + eps;
+            const T bm = beta[j] * (T(1) + qm + qm * qm) + eps;
+            const T ap = gp / (bp * bp), am = gmn / (bm * bm);
+            Ap += ap;
+            Bp += ap * p;
+            Am += am;
+            Bm += am * p;
+          }
+          incr = sp * (Bp / Ap) - sm * (Bm / Am);
+        }
+        const T dWl = lane_sum4(Rr, incr, base);  // variable l of R dU
+        if (act) Wg[(gbase + q * G + g) * 4 + l] = COMP ? w0 + (l0 + dWl) : w0 + dWl;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- K3
 // MODE 0: R = L(U).  MODE 1..3: SSP-RK3 stage s written as
 //   W(s) = W^n + c_s ((W(s-1) - W^n) + dt L(W(s-1))), c = 1, 1/4, 2/3, W(0) = W^n,

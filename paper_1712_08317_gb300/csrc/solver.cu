@@ -149,6 +149,20 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
   const T* u = static_cast<const T*>(U);
   const T* ul = static_cast<const T*>(Ulo);
   const T eps = (T)s.prm.eps, th = (T)s.prm.theta;
+  if constexpr (NV == 4) {
+    if (s.prm.characteristic) {
+      const T gg = (T)s.prm.gas_gamma;
+      if (s.nQ && (which & 1))
+        weno::dev::k_reconstruct_char<T, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
+            u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
+            (T*)wg, eps, th, gg, s.prm.linear);
+      if (s.nT && (which & 2))
+        weno::dev::k_reconstruct_char<T, 9, 6, COMP><<<grid_of(s.k1t, s.nT * 4), s.k1t.block, 0, st>>>(
+            u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
+            8 * s.nQ, (T*)wg, eps, th, gg, s.prm.linear);
+      return;
+    }
+  }
   if constexpr (COMP && NV == 4) {
     if (s.tma) {
       using TQ = weno::dev::TmaTile<12, 8>;
@@ -568,6 +582,8 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   if (p.precision != WENO_FP64 && p.precision != WENO_FP32C) return fail(WENO_EINVAL, "unknown precision");
   if (!(p.eps > 0) || !(p.theta >= 1) || (p.eqn == WENO_EQN_EULER && !(p.gas_gamma > 1)))
     return fail(WENO_EINVAL, "parameters out of range (eps > 0, theta >= 1, gamma > 1)");
+  if (p.characteristic && p.eqn != WENO_EQN_EULER)
+    return fail(WENO_EINVAL, "characteristic variables are defined for the Euler equations only");
   const Mesh& m = mesh->m;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::unique_ptr<S> s;
@@ -614,7 +630,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   int r;
   if ((r = upload(d, &d.q_slot, tq.slot, st))) return r;
   if ((r = upload(d, &d.t_slot, tt.slot, st))) return r;
-  if (d.fp64) {
+  if (d.fp64 || p.characteristic) {  // plain tables (the characteristic kernel reads these in both precisions)
     if ((r = upload_real(d, &d.q_gop, tq.gop, st))) return r;
     if ((r = upload_real(d, &d.q_dg, tq.dg, st))) return r;
     if ((r = upload_real(d, &d.q_gam, tq.gam, st))) return r;
@@ -712,7 +728,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   CK(cudaMemsetAsync(d.flag, 0, sizeof(int) * d.n_inst, st));
   if ((r = d.alloc(&d.err, sizeof(int)))) return r;
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), st));
-  if (!d.fp64 && d.nv == 4 && (r = setup_tma(d))) return r;
+  if (!d.fp64 && d.nv == 4 && !p.characteristic && (r = setup_tma(d))) return r;
   CK(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
   CK(cudaStreamSynchronize(st));
   *out = s.release();

@@ -44,11 +44,12 @@ def _case(name):
 _oracles = {}
 
 
-def _oracle(name, linear=False):
-    key = (name, linear)
+def _oracle(name, linear=False, characteristic=False):
+    key = (name, linear, characteristic)
     if key not in _oracles:
         mi, W, eqn = _case(name)
-        _oracles[key] = (mi, W, OracleSolver(OracleMesh.from_input(mi), Params(eqn=eqn, linear=linear)))
+        prm = Params(eqn=eqn, linear=linear, characteristic=characteristic)
+        _oracles[key] = (mi, W, OracleSolver(OracleMesh.from_input(mi), prm))
     return _oracles[key]
 
 
@@ -248,3 +249,61 @@ def test_invalid_arguments_return_codes():
     assert lib.weno_step(sol._h, ctypes.c_void_p(U.data_ptr()), None, 0.1, None) == _capi.WENO_EINVAL
     assert lib.weno_step(sol._h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(Ul.data_ptr()), -1.0, None) == \
         _capi.WENO_EINVAL
+
+
+EULER_CASES = [n for n in CASES if CASES[n]["eqn"] == "euler"]
+
+
+@pytest.mark.parametrize("name", EULER_CASES)
+def test_characteristic_fp64_residual_and_steps_match_oracle(name):
+    """Characteristic-variable reconstruction (Section 4), FP64: residual and 10 RK3 steps."""
+    mi, W, osol = _oracle(name, characteristic=True)
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp64", characteristic=True)
+    U, _ = sol.to_device(W)
+    assert _rel(sol.to_host(sol.residual(U)), osol.residual(W)) < TOL_FP64
+    dt = osol.max_dt(W, 0.5)
+    ref = W
+    for _ in range(10):
+        ref = osol.rk3_step(ref, dt)
+    for _ in range(10):
+        sol.step(U, None, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    assert _rel_cell(sol.to_host(U), ref) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", ["euler-mixed", "riemann-outflow", "vortex-lowq"])
+def test_characteristic_fp32c_tracks_the_oracle(name):
+    mi, W, osol = _oracle(name, characteristic=True)
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c", characteristic=True)
+    U, Ul = sol.to_device(W)
+    assert _rel(sol.to_host(sol.residual(U, Ul)), osol.residual(W)) < 2e-3
+    dt = osol.max_dt(W, 0.5)
+    ref = W
+    for _ in range(10):
+        ref = osol.rk3_step(ref, dt)
+    for _ in range(10):
+        sol.step(U, Ul, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    assert _rel_cell(sol.to_host(U, Ul), ref) < 2e-6
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32c", 1e-12)])
+def test_characteristic_conserves_and_keeps_constant_states(precision, tol):
+    mi, W, _ = _oracle("euler-mixed")
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision=precision, characteristic=True)
+    U, Ul = sol.to_device(W)
+    c0 = sol.conservation(U, Ul)[0]
+    dt = sol.max_dt(U, Ul, 0.5)[0]
+    for _ in range(5):
+        sol.step(U, Ul, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    c1 = sol.conservation(U, Ul)[0]
+    assert np.abs(c1 - c0).max() <= tol * np.abs(c0).max()
+    Wc = np.repeat(np.array([[1.2], [0.3], [-0.4], [2.9]]), W.shape[1], axis=1)
+    U, Ul = sol.to_device(Wc)
+    R = sol.to_host(sol.residual(U, Ul))
+    assert np.abs(R).max() < (1e-12 if precision == "fp64" else 1e-4)  # face closure rounding only
+
