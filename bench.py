@@ -271,7 +271,7 @@ ACC_FAMILIES = {
 }
 
 
-def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0):
+def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic=False):
     """One mesh of a convergence ladder run to t = T through the CUDA path: L1 / Linf of rho vs exact."""
     import torch
     import synthetic as S
@@ -285,7 +285,7 @@ def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0):
     area = _cell_areas(mi)
     row = {"n": n, "cells": mi.n_cells}
     for prec in precisions:
-        sol = Solver(mesh, eqn="euler", precision=prec, eps=eps)
+        sol = Solver(mesh, eqn="euler", precision=prec, eps=eps, characteristic=characteristic)
         U, Ul = sol.to_device(W0)
         dt0 = float(sol.max_dt(U, Ul, cfl)[0])
         steps = int(np.ceil(T / dt0 - 1e-12))
@@ -319,7 +319,7 @@ def run_accuracy(args):
             continue
         rows = []
         for n in ladder:
-            row = ladder_point(name, n, args.precisions.split(","), args.eps, args.cfl, T)
+            row = ladder_point(name, n, args.precisions.split(","), args.eps, args.cfl, T, args.characteristic)
             rows.append(row)
             print(json.dumps({"family": name, **row}), flush=True)
         for prec in args.precisions.split(","):
@@ -330,7 +330,8 @@ def run_accuracy(args):
                 b[prec]["order_l1"] = float(np.log(a[prec]["l1"] / b[prec]["l1"]) / np.log(r))
                 b[prec]["order_linf"] = float(np.log(a[prec]["linf"] / b[prec]["linf"]) / np.log(r))
         out[name] = rows
-    print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "eps": args.eps}), flush=True)
+    print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "eps": args.eps,
+                      "characteristic": args.characteristic}), flush=True)
 
 
 def parse_args(argv=None):
@@ -353,6 +354,7 @@ def parse_args(argv=None):
     ap.add_argument("--eps", type=float, default=1e-6, help="epsilon of the nonlinear weights (accuracy mode)")
     ap.add_argument("--cfl", type=float, default=0.5, help="CFL number of the accuracy runs")
     ap.add_argument("--precisions", default="fp64,fp32c")
+    ap.add_argument("--characteristic", action="store_true", help="accuracy mode: characteristic-variable reconstruction")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     return ap.parse_args(argv)
 
