@@ -641,6 +641,38 @@ __device__ __forceinline__ T lane_sum4(const T c[4], T x, int base) {
   return r;
 }
 
+// Roe frame of one face for lane l: row l of R^-1 (Lr) and row l of R (Rr), fields ordered
+// q_n - a, entropy, shear, q_n + a, from the two cells' averages and the outward unit normal.
+template <typename T>
+__device__ __forceinline__ void roe_rows(const T Wl[4], const T Wr[4], T nx, T ny, T gm1, int l, T Lr[4],
+                                         T Rr[4]) {
+  const T rl = Wl[0], ul = Wl[1] / rl, vl = Wl[2] / rl;
+  const T hl = (Wl[3] + gm1 * (Wl[3] - T(0.5) * rl * (ul * ul + vl * vl))) / rl;
+  const T rr = Wr[0], ur = Wr[1] / rr, vr = Wr[2] / rr;
+  const T hr = (Wr[3] + gm1 * (Wr[3] - T(0.5) * rr * (ur * ur + vr * vr))) / rr;
+  const T sl = sqrt(rl), sr = sqrt(rr), iw = T(1) / (sl + sr);
+  const T u = (sl * ul + sr * ur) * iw, v = (sl * vl + sr * vr) * iw, H = (sl * hl + sr * hr) * iw;
+  const T kin = T(0.5) * (u * u + v * v);
+  const T a = sqrt(gm1 * (H - kin)), ia = T(1) / a;
+  const T qn = u * nx + v * ny, qt = v * nx - u * ny;
+  const T b1 = gm1 * ia * ia, b2 = b1 * kin;
+  if (l == 0) {
+    Lr[0] = T(0.5) * (b2 + qn * ia); Lr[1] = T(-0.5) * (b1 * u + nx * ia);
+    Lr[2] = T(-0.5) * (b1 * v + ny * ia); Lr[3] = T(0.5) * b1;
+    Rr[0] = T(1); Rr[1] = T(1); Rr[2] = T(0); Rr[3] = T(1);
+  } else if (l == 1) {
+    Lr[0] = T(1) - b2; Lr[1] = b1 * u; Lr[2] = b1 * v; Lr[3] = -b1;
+    Rr[0] = u - a * nx; Rr[1] = u; Rr[2] = -ny; Rr[3] = u + a * nx;
+  } else if (l == 2) {
+    Lr[0] = -qt; Lr[1] = -ny; Lr[2] = nx; Lr[3] = T(0);
+    Rr[0] = v - a * ny; Rr[1] = v; Rr[2] = nx; Rr[3] = v + a * ny;
+  } else {
+    Lr[0] = T(0.5) * (b2 - qn * ia); Lr[1] = T(0.5) * (nx * ia - b1 * u);
+    Lr[2] = T(0.5) * (ny * ia - b1 * v); Lr[3] = T(0.5) * b1;
+    Rr[0] = H - a * qn; Rr[1] = kin; Rr[2] = qt; Rr[3] = H + a * qn;
+  }
+}
+
 template <typename T, int M, int G, bool COMP>
 __global__ void __launch_bounds__(256) k_reconstruct_char(
     const T* __restrict__ U, const T* __restrict__ Ulo, const int32_t* __restrict__ slot,
@@ -670,44 +702,16 @@ __global__ void __launch_bounds__(256) k_reconstruct_char(
       dW[s] = d;
     }
     const T a0 = __ldg(area + c);
-    const T gm1 = gas_gamma - T(1);
-    const T rl = W0[0], ul = W0[1] / rl, vl = W0[2] / rl;
-    const T hl = (W0[3] + gm1 * (W0[3] - T(0.5) * rl * (ul * ul + vl * vl))) / rl;
-    const T sl = sqrt(rl);
 #pragma unroll 1
     for (int k = 0; k < G / 2; ++k) {
       // face frame: Roe average with the neighbour, outward normal from the face's two Gauss points
       T Wn[4];
       load_vec<T, 4>(U + (int64_t)__ldg(slot + (int64_t)k * N + q) * 4, Wn);  // slot k+1: across face k
-      const T rr = Wn[0], ur = Wn[1] / rr, vr = Wn[2] / rr;
-      const T hr = (Wn[3] + gm1 * (Wn[3] - T(0.5) * rr * (ur * ur + vr * vr))) / rr;
-      const T sr = sqrt(rr), iw = T(1) / (sl + sr);
-      const T u = (sl * ul + sr * ur) * iw, v = (sl * vl + sr * vr) * iw, H = (sl * hl + sr * hr) * iw;
-      const T kin = T(0.5) * (u * u + v * v);
-      const T a = sqrt(gm1 * (H - kin)), ia = T(1) / a;
       const T x0 = __ldg(dg + (int64_t)(4 * k) * N + q), y0 = __ldg(dg + (int64_t)(4 * k + 1) * N + q);
       const T x1 = __ldg(dg + (int64_t)(4 * k + 2) * N + q), y1 = __ldg(dg + (int64_t)(4 * k + 3) * N + q);
       const T tx = x1 - x0, ty = y1 - y0, it = T(1) / sqrt(tx * tx + ty * ty);
-      const T nx = ty * it, ny = -tx * it;
-      const T qn = u * nx + v * ny, qt = v * nx - u * ny;
-      const T b1 = gm1 * ia * ia, b2 = b1 * kin;
-      // row l of R^-1 (fields: q_n - a, entropy, shear, q_n + a) and row l of R
       T Lr[4], Rr[4];
-      if (l == 0) {
-        Lr[0] = T(0.5) * (b2 + qn * ia); Lr[1] = T(-0.5) * (b1 * u + nx * ia);
-        Lr[2] = T(-0.5) * (b1 * v + ny * ia); Lr[3] = T(0.5) * b1;
-        Rr[0] = T(1); Rr[1] = T(1); Rr[2] = T(0); Rr[3] = T(1);
-      } else if (l == 1) {
-        Lr[0] = T(1) - b2; Lr[1] = b1 * u; Lr[2] = b1 * v; Lr[3] = -b1;
-        Rr[0] = u - a * nx; Rr[1] = u; Rr[2] = -ny; Rr[3] = u + a * nx;
-      } else if (l == 2) {
-        Lr[0] = -qt; Lr[1] = -ny; Lr[2] = nx; Lr[3] = T(0);
-        Rr[0] = v - a * ny; Rr[1] = v; Rr[2] = nx; Rr[3] = v + a * ny;
-      } else {
-        Lr[0] = T(0.5) * (b2 - qn * ia); Lr[1] = T(0.5) * (nx * ia - b1 * u);
-        Lr[2] = T(0.5) * (ny * ia - b1 * v); Lr[3] = T(0.5) * b1;
-        Rr[0] = H - a * qn; Rr[1] = kin; Rr[2] = qt; Rr[3] = H + a * qn;
-      }
+      roe_rows<T>(W0, Wn, ty * it, -tx * it, gas_gamma - T(1), l, Lr, Rr);
       // project the stencil differences onto field l, then candidate gradients and indicators
       T dU[M + 1];
       dU[0] = T(0);
@@ -763,6 +767,90 @@ __global__ void __launch_bounds__(256) k_reconstruct_char(
         }
         const T dWl = lane_sum4(Rr, incr, base);  // variable l of R dU
         if (act) Wg[(gbase + q * G + g) * 4 + l] = COMP ? w0 + (l0 + dWl) : w0 + dWl;
+      }
+    }
+  }
+}
+
+// FP32C form of the characteristic reconstruction: the packed tables of the
+// component-wise FP32C kernels (split weights precomputed in FP64) and the same
+// paired-FP32 Gauss-point arithmetic (gauss_increment) on each field.
+template <int M, int G>
+__global__ void __launch_bounds__(256) k_reconstruct_char_f32c(
+    const float* __restrict__ U, const float* __restrict__ Ulo, const int32_t* __restrict__ slot,
+    const float4* __restrict__ gop4, const float4* __restrict__ dgs, const float4* __restrict__ gpm4,
+    const float2* __restrict__ g1, const float* __restrict__ area, int64_t N, int64_t pitch, int64_t first,
+    int64_t gbase, float* __restrict__ Wg, float eps, float gas_gamma, int linear) {
+  constexpr int M4 = M / 4, P = (M + 1) / 2;
+  const int lane = threadIdx.x & 31, base = lane & ~3, l = lane & 3;
+  const int64_t total = N * 4;
+  for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < total;
+       t0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = t0 + lane;
+    const bool act = t < total;
+    const int64_t q = act ? (t >> 2) : 0;
+    const int64_t c = first + q;
+    float W0[4];
+    load_vec<float, 4>(U + c * 4, W0);
+    const float w0 = W0[l], l0 = __ldg(Ulo + c * 4 + l);
+    float dW[M + 1];
+    dW[0] = 0.f;
+#pragma unroll
+    for (int s = 1; s <= M; ++s) {
+      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
+      dW[s] = (__ldg(U + cs * 4 + l) - w0) + (__ldg(Ulo + cs * 4 + l) - l0);
+    }
+    const float a0 = __ldg(area + c);
+#pragma unroll 1
+    for (int k = 0; k < G / 2; ++k) {
+      float Wn[4];
+      load_vec<float, 4>(U + (int64_t)__ldg(slot + (int64_t)k * N + q) * 4, Wn);  // slot k+1: across face k
+      const float4 d0 = __ldg(dgs + (int64_t)(2 * k) * pitch + q), d1 = __ldg(dgs + (int64_t)(2 * k + 1) * pitch + q);
+      const float tx = d1.x - d0.x, ty = d1.y - d0.y, it = rsqrtf(tx * tx + ty * ty);
+      float Lr[4], Rr[4];
+      roe_rows<float>(W0, Wn, ty * it, -tx * it, gas_gamma - 1.f, l, Lr, Rr);
+      float dU[M + 1];
+      dU[0] = 0.f;
+#pragma unroll
+      for (int s = 1; s <= M; ++s) dU[s] = lane_sum4(Lr, dW[s], base);
+      CandPairs<P> cp;
+      float gx[2 * P], gy[2 * P], b[2 * P];
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        const float da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
+        const float4 m = __ldg(gop4 + (int64_t)j * pitch + q);
+        gx[j] = fmaf(m.x, da, m.y * db);
+        gy[j] = fmaf(m.z, da, m.w * db);
+        b[j] = a0 * fmaf(gx[j], gx[j], gy[j] * gy[j]);
+      }
+      if (M % 2) { gx[M] = 0.f; gy[M] = 0.f; b[M] = 0.f; }
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        cp.gx[p] = f2(gx[2 * p], gx[2 * p + 1]);
+        cp.gy[p] = f2(gy[2 * p], gy[2 * p + 1]);
+        cp.b[p] = f2(b[2 * p], b[2 * p + 1]);
+        cp.be[p] = __fadd2_rn(cp.b[p], f2(eps, eps));
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int g = 2 * k + h;
+        const float4 d = h ? d1 : d0;
+        float2 gp[P], gn[P];
+#pragma unroll
+        for (int kk = 0; kk < M4; ++kk) {
+          const float4 x = __ldg(gpm4 + (int64_t)(g * 2 * M4 + kk) * pitch + q);
+          const float4 y = __ldg(gpm4 + (int64_t)(g * 2 * M4 + M4 + kk) * pitch + q);
+          gp[2 * kk] = f2(x.x, x.y); gp[2 * kk + 1] = f2(x.z, x.w);
+          gn[2 * kk] = f2(y.x, y.y); gn[2 * kk + 1] = f2(y.z, y.w);
+        }
+        if (M % 4) {
+          const float2 e = __ldg(g1 + (int64_t)g * pitch + q);
+          gp[P - 1] = f2(e.x, 0.f);
+          gn[P - 1] = f2(e.y, 0.f);
+        }
+        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
+        const float dWl = lane_sum4(Rr, incr, base);  // variable l of R dU
+        if (act) Wg[(gbase + q * G + g) * 4 + l] = w0 + (l0 + dWl);
       }
     }
   }

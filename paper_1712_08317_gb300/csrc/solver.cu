@@ -152,14 +152,27 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
   if constexpr (NV == 4) {
     if (s.prm.characteristic) {
       const T gg = (T)s.prm.gas_gamma;
-      if (s.nQ && (which & 1))
-        weno::dev::k_reconstruct_char<T, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
-            u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
-            (T*)wg, eps, th, gg, s.prm.linear);
-      if (s.nT && (which & 2))
-        weno::dev::k_reconstruct_char<T, 9, 6, COMP><<<grid_of(s.k1t, s.nT * 4), s.k1t.block, 0, st>>>(
-            u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
-            8 * s.nQ, (T*)wg, eps, th, gg, s.prm.linear);
+      if constexpr (COMP) {  // packed FP32C tables, paired-FP32 weights
+        if (s.nQ && (which & 1))
+          weno::dev::k_reconstruct_char_f32c<12, 8><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
+              u, ul, s.q_slot, (const float4*)s.q_gop, (const float4*)s.q_dg, (const float4*)s.q_gam,
+              (const float2*)s.q_gam1, (const float*)s.area, s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, gg,
+              s.prm.linear);
+        if (s.nT && (which & 2))
+          weno::dev::k_reconstruct_char_f32c<9, 6><<<grid_of(s.k1t, s.nT * 4), s.k1t.block, 0, st>>>(
+              u, ul, s.t_slot, (const float4*)s.t_gop, (const float4*)s.t_dg, (const float4*)s.t_gam,
+              (const float2*)s.t_gam1, (const float*)s.area, s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, gg,
+              s.prm.linear);
+      } else {
+        if (s.nQ && (which & 1))
+          weno::dev::k_reconstruct_char<T, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
+              u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0,
+              0, (T*)wg, eps, th, gg, s.prm.linear);
+        if (s.nT && (which & 2))
+          weno::dev::k_reconstruct_char<T, 9, 6, COMP><<<grid_of(s.k1t, s.nT * 4), s.k1t.block, 0, st>>>(
+              u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT,
+              s.nQ, 8 * s.nQ, (T*)wg, eps, th, gg, s.prm.linear);
+      }
       return;
     }
   }
@@ -630,7 +643,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   int r;
   if ((r = upload(d, &d.q_slot, tq.slot, st))) return r;
   if ((r = upload(d, &d.t_slot, tt.slot, st))) return r;
-  if (d.fp64 || p.characteristic) {  // plain tables (the characteristic kernel reads these in both precisions)
+  if (d.fp64) {
     if ((r = upload_real(d, &d.q_gop, tq.gop, st))) return r;
     if ((r = upload_real(d, &d.q_dg, tq.dg, st))) return r;
     if ((r = upload_real(d, &d.q_gam, tq.gam, st))) return r;
