@@ -271,7 +271,7 @@ ACC_FAMILIES = {
 }
 
 
-def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic=False):
+def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic=False, optimize=True):
     """One mesh of a convergence ladder run to t = T through the CUDA path: L1 / Linf of rho vs exact."""
     import torch
     import synthetic as S
@@ -285,7 +285,7 @@ def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic
     area = _cell_areas(mi)
     row = {"n": n, "cells": mi.n_cells}
     for prec in precisions:
-        sol = Solver(mesh, eqn="euler", precision=prec, eps=eps, characteristic=characteristic)
+        sol = Solver(mesh, eqn="euler", precision=prec, eps=eps, characteristic=characteristic, optimize=optimize)
         U, Ul = sol.to_device(W0)
         dt0 = float(sol.max_dt(U, Ul, cfl)[0])
         steps = int(np.ceil(T / dt0 - 1e-12))
@@ -319,7 +319,8 @@ def run_accuracy(args):
             continue
         rows = []
         for n in ladder:
-            row = ladder_point(name, n, args.precisions.split(","), args.eps, args.cfl, T, args.characteristic)
+            row = ladder_point(name, n, args.precisions.split(","), args.eps, args.cfl, T, args.characteristic,
+                               not args.raw_weights)
             rows.append(row)
             print(json.dumps({"family": name, **row}), flush=True)
         for prec in args.precisions.split(","):
@@ -331,7 +332,7 @@ def run_accuracy(args):
                 b[prec]["order_linf"] = float(np.log(a[prec]["linf"] / b[prec]["linf"]) / np.log(r))
         out[name] = rows
     print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "eps": args.eps,
-                      "characteristic": args.characteristic}), flush=True)
+                      "characteristic": args.characteristic, "optimized_weights": not args.raw_weights}), flush=True)
 
 
 def parse_args(argv=None):
@@ -355,6 +356,7 @@ def parse_args(argv=None):
     ap.add_argument("--cfl", type=float, default=0.5, help="CFL number of the accuracy runs")
     ap.add_argument("--precisions", default="fp64,fp32c")
     ap.add_argument("--characteristic", action="store_true", help="accuracy mode: characteristic-variable reconstruction")
+    ap.add_argument("--raw-weights", action="store_true", help="accuracy mode: linear weights without the optimisation")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     return ap.parse_args(argv)
 

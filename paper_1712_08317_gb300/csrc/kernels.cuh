@@ -772,11 +772,15 @@ __global__ void __launch_bounds__(256) k_reconstruct_char(
   }
 }
 
+#ifndef WENO_KCHAR_MIN_BLOCKS
+#define WENO_KCHAR_MIN_BLOCKS 2  // resident 256-thread blocks per SM the characteristic kernel's registers allow
+#endif
+
 // FP32C form of the characteristic reconstruction: the packed tables of the
 // component-wise FP32C kernels (split weights precomputed in FP64) and the same
 // paired-FP32 Gauss-point arithmetic (gauss_increment) on each field.
 template <int M, int G>
-__global__ void __launch_bounds__(256) k_reconstruct_char_f32c(
+__global__ void __launch_bounds__(256, WENO_KCHAR_MIN_BLOCKS) k_reconstruct_char_f32c(
     const float* __restrict__ U, const float* __restrict__ Ulo, const int32_t* __restrict__ slot,
     const float4* __restrict__ gop4, const float4* __restrict__ dgs, const float4* __restrict__ gpm4,
     const float2* __restrict__ g1, const float* __restrict__ area, int64_t N, int64_t pitch, int64_t first,

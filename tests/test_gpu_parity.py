@@ -44,11 +44,11 @@ def _case(name):
 _oracles = {}
 
 
-def _oracle(name, linear=False, characteristic=False):
-    key = (name, linear, characteristic)
+def _oracle(name, linear=False, characteristic=False, optimize=True):
+    key = (name, linear, characteristic, optimize)
     if key not in _oracles:
         mi, W, eqn = _case(name)
-        prm = Params(eqn=eqn, linear=linear, characteristic=characteristic)
+        prm = Params(eqn=eqn, linear=linear, characteristic=characteristic, optimize=optimize)
         _oracles[key] = (mi, W, OracleSolver(OracleMesh.from_input(mi), prm))
     return _oracles[key]
 
@@ -306,4 +306,19 @@ def test_characteristic_conserves_and_keeps_constant_states(precision, tol):
     U, Ul = sol.to_device(Wc)
     R = sol.to_host(sol.residual(U, Ul))
     assert np.abs(R).max() < (1e-12 if precision == "fp64" else 1e-4)  # face closure rounding only
+
+
+@pytest.mark.parametrize("name", ["vortex-lowq", "euler-mixed", "scalar-quad"])
+def test_raw_linear_weights_match_oracle(name):
+    """Section 3.3 switched off (raw minimum-norm weights, which reach large values on
+    low-quality meshes): FP64 residual and FP32C tracking."""
+    mi, W, osol = _oracle(name, optimize=False)
+    ref = osol.residual(W)
+    eqn = osol.params.eqn
+    sol = Solver(Mesh.from_input(mi), eqn=eqn, precision="fp64", optimize=False)
+    U, _ = sol.to_device(W)
+    assert _rel(sol.to_host(sol.residual(U)), ref) < TOL_FP64
+    s32 = Solver(Mesh.from_input(mi), eqn=eqn, precision="fp32c", optimize=False)
+    U, Ul = s32.to_device(W)
+    assert _rel(s32.to_host(s32.residual(U, Ul)), ref) < 2e-3
 
