@@ -308,7 +308,24 @@ def test_characteristic_conserves_and_keeps_constant_states(precision, tol):
     assert np.abs(R).max() < (1e-12 if precision == "fp64" else 1e-4)  # face closure rounding only
 
 
-@pytest.mark.parametrize("name", ["vortex-lowq", "euler-mixed", "scalar-quad"])
+def test_raw_linear_weights_on_the_low_quality_mesh_are_flagged_like_the_oracle():
+    """Without Section 3.3 the weights on the aspect-ratio-10 vortex mesh are large enough that
+    the very first reconstruction has negative pressure or density at some Gauss points: the
+    oracle raises and both GPU precisions report WENO_ENONPHYS."""
+    from oracle.scheme import NonPhysicalState
+    mi, W, osol = _oracle("vortex-lowq", optimize=False)
+    with pytest.raises(NonPhysicalState):
+        osol.residual(W)
+    for precision in ("fp64", "fp32c"):
+        sol = Solver(Mesh.from_input(mi), eqn="euler", precision=precision, optimize=False)
+        U, Ul = sol.to_device(W)
+        sol.residual(U, Ul)
+        with pytest.raises(_capi.WenoError) as e:
+            sol.check()
+        assert e.value.code == _capi.WENO_ENONPHYS
+
+
+@pytest.mark.parametrize("name", ["euler-mixed", "scalar-quad", "riemann-outflow"])
 def test_raw_linear_weights_match_oracle(name):
     """Section 3.3 switched off (raw minimum-norm weights, which reach large values on
     low-quality meshes): FP64 residual and FP32C tracking."""
