@@ -332,9 +332,13 @@ def test_raw_linear_weights_match_oracle(name):
     mi, W, osol = _oracle(name, optimize=False)
     ref = osol.residual(W)
     eqn = osol.params.eqn
+    # the two sides' minimum-norm solves differ at rounding level; the raw weights multiply
+    # that difference by their size (max |gamma| 552 raw vs 6.8 optimised on the split meshes)
+    raw, opt = Mesh.from_input(mi).weight_stats()
+    tol = TOL_FP64 * max(1.0, raw.max() / opt.max())
     sol = Solver(Mesh.from_input(mi), eqn=eqn, precision="fp64", optimize=False)
     U, _ = sol.to_device(W)
-    assert _rel(sol.to_host(sol.residual(U)), ref) < TOL_FP64
+    assert _rel(sol.to_host(sol.residual(U)), ref) < tol
     s32 = Solver(Mesh.from_input(mi), eqn=eqn, precision="fp32c", optimize=False)
     U, Ul = s32.to_device(W)
     assert _rel(s32.to_host(s32.residual(U, Ul)), ref) < 2e-3
