@@ -258,6 +258,17 @@ def k1_ops(nQ, nT, nv=4):
     return nQ * per(12, 8) + nT * per(9, 6)
 
 
+def k1_ops_char(nQ, nT):
+    """Algorithmic FP32 operations (FMA = 1) of one characteristic-variable reconstruction pass:
+    per (cell, field) 3 per stencil slot (Delta W); per face the Roe frame (60), the projection of
+    the slot differences onto the field (4 per slot) and the field's candidate gradients and
+    indicators (8 per candidate); per Gauss point the weights (16 per candidate + 10) and the
+    back-projection (4)."""
+    def per(M, G):
+        return 4 * (3 * M + (G // 2) * (60 + 4 * M + 8 * M) + G * (16 * M + 14))
+    return nQ * per(12, 8) + nT * per(9, 6)
+
+
 def _cell_areas(mi):
     cells, cnt = mi.padded_cells()
     P = mi.nodes[cells]
@@ -549,9 +560,24 @@ def main():
         torch.cuda.synchronize()
         char_ms = max_over_ranks(dist, h0.elapsed_time(h1), dev)
         solc.check()
+        solc.run_pass(1, Uc, Ulc)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(reps):
+            solc.run_pass(1, Uc, Ulc)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        char_k1 = p0.elapsed_time(p1) / reps
+        char_ops = k1_ops_char(nQ, nT)
         char = {"value": whole_job_rate(ws, N, 3 * args.char_steps, char_ms), "unit": UNIT,
                 "steps": args.char_steps, "ms_per_step": char_ms / args.char_steps, "precision": "fp32c",
-                "reconstruction": "characteristic variables (Roe-averaged normal Jacobian per face)"}
+                "reconstruction": "characteristic variables (Roe-averaged normal Jacobian per face)",
+                "roofline": {"kernel": "k_reconstruct_char_f32c (quad + triangle launches of one pass)",
+                             "bound": "alu", "achieved": char_ops / (char_k1 / 1e3) / 1e12, "peak": alu_peak,
+                             "unit": "Top/s (FP32 lane ops, FMA = 1)",
+                             "frac": char_ops / (char_k1 / 1e3) / 1e12 / alu_peak,
+                             "algorithmic_ops_per_launch": char_ops, "ms_per_launch": char_k1}}
         del solc, Uc, Ulc
         torch.cuda.empty_cache()
 
