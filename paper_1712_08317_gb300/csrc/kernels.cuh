@@ -860,6 +860,142 @@ __global__ void __launch_bounds__(256, WENO_KCHAR_MIN_BLOCKS) k_reconstruct_char
   }
 }
 
+// FP32C characteristic reconstruction with the tile's tables (split weights,
+// Gauss offsets and sigma+-, gradient operators) staged in shared memory by TMA,
+// as in k_reconstruct_tma: the per-face re-reads of the gradient operators and
+// the per-point weights come from shared memory.  Lanes of cells past the end
+// compute on the last cell's data and store nothing.
+template <int M, int G>
+struct CharTile {
+  static constexpr int TILE = WENO_K1_TILE;
+  static constexpr int THREADS = TILE * 4;
+  static constexpr int M4 = M / 4;
+  static constexpr int GPM = G * 2 * M4 * TILE * 16;
+  static constexpr int DGS = G * TILE * 16;
+  static constexpr int G1 = (M % 4) ? G * TILE * 8 : 0;
+  static constexpr int GOP = M * TILE * 16;                    // D_j^+ rows
+  static constexpr int STAGE = GPM + DGS + G1 + GOP;           // bytes, multiple of 128
+  static constexpr int SMEM = STAGE + 16;                      // one buffer + one mbarrier (padded)
+};
+
+template <int M, int G>
+__global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 / WENO_K1_TILE)
+    k_reconstruct_char_tma(const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
+                           const __grid_constant__ CUtensorMap map_g1, const __grid_constant__ CUtensorMap map_gop,
+                           const float* __restrict__ U, const float* __restrict__ Ulo,
+                           const int32_t* __restrict__ slot, const float* __restrict__ area, int64_t N,
+                           int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, float gas_gamma,
+                           int linear, int* __restrict__ err, int stall) {
+  using L = CharTile<M, G>;
+  constexpr int P = (M + 1) / 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::STAGE);
+  const int tid = threadIdx.x, base = (tid & 31) & ~3, l = tid & 3, cl = tid >> 2;
+  const int64_t ntiles = (N + L::TILE - 1) / L::TILE;
+  if (tid == 0) {
+    mbar_init(&bar[0], stall ? 2 : 1);  // stall != 0 (testing aid): the wait runs out
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tile) {
+    mbar_expect_tx(&bar[0], L::STAGE);
+    tma_load_2d(smem, &map_gpm, (int)(tile * L::TILE * 4), 0, &bar[0]);
+    tma_load_2d(smem + L::GPM, &map_dgs, (int)(tile * L::TILE * 4), 0, &bar[0]);
+    if (M % 4) tma_load_2d(smem + L::GPM + L::DGS, &map_g1, (int)(tile * L::TILE * 2), 0, &bar[0]);
+    tma_load_2d(smem + L::GPM + L::DGS + L::G1, &map_gop, (int)(tile * L::TILE * 4), 0, &bar[0]);
+  };
+  int64_t tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile);
+  uint32_t phase = 0u;
+  const float4* sgp = reinterpret_cast<const float4*>(smem);
+  const float4* sds = reinterpret_cast<const float4*>(smem + L::GPM);
+  const float2* sg1 = reinterpret_cast<const float2*>(smem + L::GPM + L::DGS);
+  const float4* sgo = reinterpret_cast<const float4*>(smem + L::GPM + L::DGS + L::G1);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x;
+    const int64_t qr = tile * L::TILE + cl;
+    const bool act = qr < N;
+    const int64_t q = act ? qr : N - 1;
+    const int64_t c = first + q;
+    // stencil gathers (independent of the staged tables) before the wait
+    float W0[4];
+    load_vec<float, 4>(U + c * 4, W0);
+    const float w0 = W0[l], l0 = __ldg(Ulo + c * 4 + l);
+    float dW[M + 1];
+    dW[0] = 0.f;
+#pragma unroll
+    for (int s = 1; s <= M; ++s) {
+      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
+      dW[s] = (__ldg(U + cs * 4 + l) - w0) + (__ldg(Ulo + cs * 4 + l) - l0);
+    }
+    const float a0 = __ldg(area + c);
+    const bool ok = mbar_wait_bounded(&bar[0], phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) *err = 1;
+      return;
+    }
+#pragma unroll 1
+    for (int k = 0; k < G / 2; ++k) {
+      float Wn[4];
+      load_vec<float, 4>(U + (int64_t)__ldg(slot + (int64_t)k * N + q) * 4, Wn);  // slot k+1: across face k
+      const float4 d0 = sds[(2 * k) * L::TILE + cl], d1 = sds[(2 * k + 1) * L::TILE + cl];
+      const float tx = d1.x - d0.x, ty = d1.y - d0.y, it = rsqrtf(tx * tx + ty * ty);
+      float Lr[4], Rr[4];
+      roe_rows<float>(W0, Wn, ty * it, -tx * it, gas_gamma - 1.f, l, Lr, Rr);
+      float dU[M + 1];
+      dU[0] = 0.f;
+#pragma unroll
+      for (int s = 1; s <= M; ++s) dU[s] = lane_sum4(Lr, dW[s], base);
+      CandPairs<P> cp;
+      float gx[2 * P], gy[2 * P], b[2 * P];
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        const float da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
+        const float4 m = sgo[j * L::TILE + cl];
+        gx[j] = fmaf(m.x, da, m.y * db);
+        gy[j] = fmaf(m.z, da, m.w * db);
+        b[j] = a0 * fmaf(gx[j], gx[j], gy[j] * gy[j]);
+      }
+      if (M % 2) { gx[M] = 0.f; gy[M] = 0.f; b[M] = 0.f; }
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        cp.gx[p] = f2(gx[2 * p], gx[2 * p + 1]);
+        cp.gy[p] = f2(gy[2 * p], gy[2 * p + 1]);
+        cp.b[p] = f2(b[2 * p], b[2 * p + 1]);
+        cp.be[p] = __fadd2_rn(cp.b[p], f2(eps, eps));
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int g = 2 * k + h;
+        const float4 d = h ? d1 : d0;
+        float2 gp[P], gn[P];
+#pragma unroll
+        for (int kk = 0; kk < L::M4; ++kk) {
+          const float4 x = sgp[(g * 2 * L::M4 + kk) * L::TILE + cl];
+          const float4 y = sgp[(g * 2 * L::M4 + L::M4 + kk) * L::TILE + cl];
+          gp[2 * kk] = f2(x.x, x.y); gp[2 * kk + 1] = f2(x.z, x.w);
+          gn[2 * kk] = f2(y.x, y.y); gn[2 * kk + 1] = f2(y.z, y.w);
+        }
+        if (M % 4) {
+          const float2 e = sg1[g * L::TILE + cl];
+          gp[P - 1] = f2(e.x, 0.f);
+          gn[P - 1] = f2(e.y, 0.f);
+        }
+        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
+        const float dWl = lane_sum4(Rr, incr, base);
+        if (act) Wg[(gbase + q * G + g) * 4 + l] = w0 + (l0 + dWl);
+      }
+    }
+    __syncthreads();  // the buffer is free for the next tile's copy
+    if (tid == 0 && next < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(next);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- K3
 // MODE 0: R = L(U).  MODE 1..3: SSP-RK3 stage s written as
 //   W(s) = W^n + c_s ((W(s-1) - W^n) + dt L(W(s-1))), c = 1, 1/4, 2/3, W(0) = W^n,

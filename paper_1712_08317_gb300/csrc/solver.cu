@@ -89,6 +89,7 @@ struct weno_solver_s {
   int64_t q_pitch = 0, t_pitch = 0;  // row pitch (cells) of the packed FP32C tables
   bool tma = false;                   // Euler FP32C: reconstruction with TMA-staged tables
   CUtensorMap q_map_gpm{}, q_map_dgs{}, t_map_gpm{}, t_map_dgs{}, t_map_g1{};
+  CUtensorMap q_map_gop{}, t_map_gop{};  // gradient operators (characteristic reconstruction)
   int* err = nullptr;                 // set by a kernel whose bounded wait timed out
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
   void *area = nullptr, *inv_area = nullptr, *inv_area_lo = nullptr;
@@ -153,6 +154,19 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
     if (s.prm.characteristic) {
       const T gg = (T)s.prm.gas_gamma;
       if constexpr (COMP) {  // packed FP32C tables, paired-FP32 weights
+        if (s.tma) {
+          using CQ = weno::dev::CharTile<12, 8>;
+          using CT = weno::dev::CharTile<9, 6>;
+          if (s.nQ && (which & 1))
+            weno::dev::k_reconstruct_char_tma<12, 8><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
+                s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0,
+                0, (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
+          if (s.nT && (which & 2))
+            weno::dev::k_reconstruct_char_tma<9, 6><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
+                s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT,
+                s.nQ, 8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
+          return;
+        }
         if (s.nQ && (which & 1))
           weno::dev::k_reconstruct_char_f32c<12, 8><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
               u, ul, s.q_slot, (const float4*)s.q_gop, (const float4*)s.q_dg, (const float4*)s.q_gam,
@@ -426,6 +440,17 @@ int setup_tma(S& s) {
   }
   CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TQ::SMEM));
   CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM));
+  if (s.prm.characteristic) {
+    // D_j^+ rows: M float4 rows
+    if (s.nQ && (r = make_map_2d(enc, &s.q_map_gop, s.q_gop, 4 * s.q_pitch, 12, 16 * s.q_pitch, 4 * kTile, 12)))
+      return r;
+    if (s.nT && (r = make_map_2d(enc, &s.t_map_gop, s.t_gop, 4 * s.t_pitch, 9, 16 * s.t_pitch, 4 * kTile, 9)))
+      return r;
+    CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_char_tma<12, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            weno::dev::CharTile<12, 8>::SMEM));
+    CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_char_tma<9, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            weno::dev::CharTile<9, 6>::SMEM));
+  }
   s.tma = true;
   return WENO_OK;
 }
@@ -741,7 +766,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   CK(cudaMemsetAsync(d.flag, 0, sizeof(int) * d.n_inst, st));
   if ((r = d.alloc(&d.err, sizeof(int)))) return r;
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), st));
-  if (!d.fp64 && d.nv == 4 && !p.characteristic && (r = setup_tma(d))) return r;
+  if (!d.fp64 && d.nv == 4 && (r = setup_tma(d))) return r;
   CK(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
   CK(cudaStreamSynchronize(st));
   *out = s.release();

@@ -205,9 +205,10 @@ def test_nonphysical_flags_name_the_instance(precision):
     assert e.value.code == _capi.WENO_ENONPHYS and "1 of 3" in str(e.value)
 
 
-def test_bounded_wait_reports_timeout_and_context_survives():
+@pytest.mark.parametrize("characteristic", [False, True])
+def test_bounded_wait_reports_timeout_and_context_survives(characteristic):
     mi, W, _ = _oracle("euler-mixed")
-    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c")
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c", characteristic=characteristic)
     U, Ul = sol.to_device(W)
     R0 = sol.residual(U, Ul).clone()
     sol.check()
