@@ -776,90 +776,6 @@ __global__ void __launch_bounds__(256) k_reconstruct_char(
 #define WENO_KCHAR_MIN_BLOCKS 2  // resident 256-thread blocks per SM the characteristic kernel's registers allow
 #endif
 
-// FP32C form of the characteristic reconstruction: the packed tables of the
-// component-wise FP32C kernels (split weights precomputed in FP64) and the same
-// paired-FP32 Gauss-point arithmetic (gauss_increment) on each field.
-template <int M, int G>
-__global__ void __launch_bounds__(256, WENO_KCHAR_MIN_BLOCKS) k_reconstruct_char_f32c(
-    const float* __restrict__ U, const float* __restrict__ Ulo, const int32_t* __restrict__ slot,
-    const float4* __restrict__ gop4, const float4* __restrict__ dgs, const float4* __restrict__ gpm4,
-    const float2* __restrict__ g1, const float* __restrict__ area, int64_t N, int64_t pitch, int64_t first,
-    int64_t gbase, float* __restrict__ Wg, float eps, float gas_gamma, int linear) {
-  constexpr int M4 = M / 4, P = (M + 1) / 2;
-  const int lane = threadIdx.x & 31, base = lane & ~3, l = lane & 3;
-  const int64_t total = N * 4;
-  for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < total;
-       t0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = t0 + lane;
-    const bool act = t < total;
-    const int64_t q = act ? (t >> 2) : 0;
-    const int64_t c = first + q;
-    float W0[4];
-    load_vec<float, 4>(U + c * 4, W0);
-    const float w0 = W0[l], l0 = __ldg(Ulo + c * 4 + l);
-    float dW[M + 1];
-    dW[0] = 0.f;
-#pragma unroll
-    for (int s = 1; s <= M; ++s) {
-      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
-      dW[s] = (__ldg(U + cs * 4 + l) - w0) + (__ldg(Ulo + cs * 4 + l) - l0);
-    }
-    const float a0 = __ldg(area + c);
-#pragma unroll 1
-    for (int k = 0; k < G / 2; ++k) {
-      float Wn[4];
-      load_vec<float, 4>(U + (int64_t)__ldg(slot + (int64_t)k * N + q) * 4, Wn);  // slot k+1: across face k
-      const float4 d0 = __ldg(dgs + (int64_t)(2 * k) * pitch + q), d1 = __ldg(dgs + (int64_t)(2 * k + 1) * pitch + q);
-      const float tx = d1.x - d0.x, ty = d1.y - d0.y, it = rsqrtf(tx * tx + ty * ty);
-      float Lr[4], Rr[4];
-      roe_rows<float>(W0, Wn, ty * it, -tx * it, gas_gamma - 1.f, l, Lr, Rr);
-      float dU[M + 1];
-      dU[0] = 0.f;
-#pragma unroll
-      for (int s = 1; s <= M; ++s) dU[s] = lane_sum4(Lr, dW[s], base);
-      CandPairs<P> cp;
-      float gx[2 * P], gy[2 * P], b[2 * P];
-#pragma unroll
-      for (int j = 0; j < M; ++j) {
-        const float da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
-        const float4 m = __ldg(gop4 + (int64_t)j * pitch + q);
-        gx[j] = fmaf(m.x, da, m.y * db);
-        gy[j] = fmaf(m.z, da, m.w * db);
-        b[j] = a0 * fmaf(gx[j], gx[j], gy[j] * gy[j]);
-      }
-      if (M % 2) { gx[M] = 0.f; gy[M] = 0.f; b[M] = 0.f; }
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        cp.gx[p] = f2(gx[2 * p], gx[2 * p + 1]);
-        cp.gy[p] = f2(gy[2 * p], gy[2 * p + 1]);
-        cp.b[p] = f2(b[2 * p], b[2 * p + 1]);
-        cp.be[p] = __fadd2_rn(cp.b[p], f2(eps, eps));
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int g = 2 * k + h;
-        const float4 d = h ? d1 : d0;
-        float2 gp[P], gn[P];
-#pragma unroll
-        for (int kk = 0; kk < M4; ++kk) {
-          const float4 x = __ldg(gpm4 + (int64_t)(g * 2 * M4 + kk) * pitch + q);
-          const float4 y = __ldg(gpm4 + (int64_t)(g * 2 * M4 + M4 + kk) * pitch + q);
-          gp[2 * kk] = f2(x.x, x.y); gp[2 * kk + 1] = f2(x.z, x.w);
-          gn[2 * kk] = f2(y.x, y.y); gn[2 * kk + 1] = f2(y.z, y.w);
-        }
-        if (M % 4) {
-          const float2 e = __ldg(g1 + (int64_t)g * pitch + q);
-          gp[P - 1] = f2(e.x, 0.f);
-          gn[P - 1] = f2(e.y, 0.f);
-        }
-        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
-        const float dWl = lane_sum4(Rr, incr, base);  // variable l of R dU
-        if (act) Wg[(gbase + q * G + g) * 4 + l] = w0 + (l0 + dWl);
-      }
-    }
-  }
-}
-
 // FP32C characteristic reconstruction with the tile's tables (split weights,
 // Gauss offsets and sigma+-, gradient operators) staged in shared memory by TMA,
 // as in k_reconstruct_tma: the per-face re-reads of the gradient operators and

@@ -153,30 +153,17 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
   if constexpr (NV == 4) {
     if (s.prm.characteristic) {
       const T gg = (T)s.prm.gas_gamma;
-      if constexpr (COMP) {  // packed FP32C tables, paired-FP32 weights
-        if (s.tma) {
-          using CQ = weno::dev::CharTile<12, 8>;
-          using CT = weno::dev::CharTile<9, 6>;
-          if (s.nQ && (which & 1))
-            weno::dev::k_reconstruct_char_tma<12, 8><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
-                s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0,
-                0, (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
-          if (s.nT && (which & 2))
-            weno::dev::k_reconstruct_char_tma<9, 6><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
-                s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT,
-                s.nQ, 8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
-          return;
-        }
+      if constexpr (COMP) {  // packed FP32C tables staged by TMA (setup_tma runs for every FP32C Euler solver)
+        using CQ = weno::dev::CharTile<12, 8>;
+        using CT = weno::dev::CharTile<9, 6>;
         if (s.nQ && (which & 1))
-          weno::dev::k_reconstruct_char_f32c<12, 8><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
-              u, ul, s.q_slot, (const float4*)s.q_gop, (const float4*)s.q_dg, (const float4*)s.q_gam,
-              (const float2*)s.q_gam1, (const float*)s.area, s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, gg,
-              s.prm.linear);
+          weno::dev::k_reconstruct_char_tma<12, 8><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
+              s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
+              (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
         if (s.nT && (which & 2))
-          weno::dev::k_reconstruct_char_f32c<9, 6><<<grid_of(s.k1t, s.nT * 4), s.k1t.block, 0, st>>>(
-              u, ul, s.t_slot, (const float4*)s.t_gop, (const float4*)s.t_dg, (const float4*)s.t_gam,
-              (const float2*)s.t_gam1, (const float*)s.area, s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, gg,
-              s.prm.linear);
+          weno::dev::k_reconstruct_char_tma<9, 6><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
+              s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
+              8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
       } else {
         if (s.nQ && (which & 1))
           weno::dev::k_reconstruct_char<T, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
