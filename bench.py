@@ -573,7 +573,7 @@ def main():
         char = {"value": whole_job_rate(ws, N, 3 * args.char_steps, char_ms), "unit": UNIT,
                 "steps": args.char_steps, "ms_per_step": char_ms / args.char_steps, "precision": "fp32c",
                 "reconstruction": "characteristic variables (Roe-averaged normal Jacobian per face)",
-                "roofline": {"kernel": "k_reconstruct_char_f32c (quad + triangle launches of one pass)",
+                "roofline": {"kernel": "k_reconstruct_char_tma (quad + triangle launches of one pass)",
                              "bound": "alu", "achieved": char_ops / (char_k1 / 1e3) / 1e12, "peak": alu_peak,
                              "unit": "Top/s (FP32 lane ops, FMA = 1)",
                              "frac": char_ops / (char_k1 / 1e3) / 1e12 / alu_peak,
