@@ -250,6 +250,12 @@ def test_invalid_arguments_return_codes():
     assert lib.weno_step(sol._h, ctypes.c_void_p(U.data_ptr()), None, 0.1, None) == _capi.WENO_EINVAL
     assert lib.weno_step(sol._h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(Ul.data_ptr()), -1.0, None) == \
         _capi.WENO_EINVAL
+    # characteristic variables are defined for the Euler equations only; theta < 1 and eps <= 0 are rejected
+    mesh = Mesh.from_input(mi)
+    for bad in (dict(eqn="scalar", characteristic=True), dict(theta=0.5), dict(eps=0.0)):
+        with pytest.raises(_capi.WenoError) as e:
+            Solver(mesh, precision="fp32c", **bad)
+        assert e.value.code == _capi.WENO_EINVAL
 
 
 EULER_CASES = [n for n in CASES if CASES[n]["eqn"] == "euler"]
