@@ -67,7 +67,8 @@ def _signed_area(p: np.ndarray) -> float:
 class OracleMesh:
     """Topology + geometry + stencils of a 2D mesh of triangles and quadrilaterals."""
 
-    def __init__(self, nodes, cell_ptr, cell_nodes, bc="periodic", origin=(0.0, 0.0), extent=(1.0, 1.0)):
+    def __init__(self, nodes, cell_ptr, cell_nodes, bc="periodic", origin=(0.0, 0.0), extent=(1.0, 1.0),
+                 walls=()):
         self.nodes = np.asarray(nodes, dtype=np.float64)
         cell_ptr = np.asarray(cell_ptr, dtype=np.int64)
         cell_nodes = np.asarray(cell_nodes, dtype=np.int64)
@@ -75,15 +76,53 @@ class OracleMesh:
         self.origin = tuple(float(v) for v in origin)
         self.extent = tuple(float(v) for v in extent)
         self.n_cells = int(cell_ptr.shape[0] - 1)
+        self.walls = frozenset(int(w) for w in walls)
+        if self.walls and bc == "periodic":
+            raise MeshError("walls are sides of an outflow box")
         self._orient_cells(cell_ptr, cell_nodes)
         self._node_classes()
         self._faces()
         self._cell_geometry()
+        self._face_sides()
         self._stencils()
 
     @classmethod
     def from_input(cls, m):
-        return cls(m.nodes, m.cell_ptr, m.cell_nodes, m.bc, m.origin, m.extent)
+        return cls(m.nodes, m.cell_ptr, m.cell_nodes, m.bc, m.origin, m.extent, getattr(m, "walls", ()))
+
+    def _face_sides(self):
+        """Box side of every boundary face (-1 elsewhere) and whether it is a reflective wall."""
+        self.face_side = np.full(self.n_faces, -1, dtype=np.int64)
+        lo, ext = np.array(self.origin), np.array(self.extent)
+        tol = 1e-9 * ext.max()
+        for f in np.flatnonzero(self.face_R < 0):
+            a, b = self.face_line(f)
+            m = 0.5 * (a + b)
+            for side, (axis, val) in enumerate(((0, lo[0]), (0, lo[0] + ext[0]), (1, lo[1]), (1, lo[1] + ext[1]))):
+                if abs(a[axis] - val) <= tol and abs(b[axis] - val) <= tol and abs(m[axis] - val) <= tol:
+                    self.face_side[f] = side
+        self.face_wall = np.array([s in self.walls for s in self.face_side], dtype=bool)
+
+    def reflect_momentum(self, W, fx, fy):
+        """State with its x (y) momentum reversed where fx (fy) is set (reflection across a wall parallel
+        to the y (x) axis)."""
+        W = np.array(W, dtype=np.float64, copy=True)
+        W[1] = np.where(fx, -W[1], W[1])
+        W[2] = np.where(fy, -W[2], W[2])
+        return W
+
+    def slot_flips(self, c: int, j: int):
+        """(fx, fy): momentum components reversed in the value of slot j of cell c (mirror images
+        across reflective walls; an image across two walls reverses both or, for parallel walls, none)."""
+        _, _, _, _, refl = self.slots[c][self.resolve(c, j)]
+        fx = fy = 0
+        for f in refl:
+            if self.face_wall[f]:
+                if self.face_side[f] < 2:
+                    fx ^= 1
+                else:
+                    fy ^= 1
+        return fx, fy
 
     # ------------------------------------------------------------------ topology
     def _orient_cells(self, cell_ptr, cell_nodes):

@@ -67,6 +67,7 @@ class GroupTables:
     G: int
     area: np.ndarray       # (N,)
     members: np.ndarray    # (N, M, 2) cells whose averages candidate j reads (S_j1, S_j2)
+    member_flip: np.ndarray  # (N, M, 2, 2) momentum components (x, y) reversed in those values (walls)
     grad_op: np.ndarray    # (N, M, 2, 2) g_j = grad_op[j] @ (dW_S1, dW_S2)
     dG: np.ndarray         # (N, G, 2) x_G - c0
     gamma: np.ndarray      # (N, G, M) linear weights used at run time
@@ -169,6 +170,8 @@ def _group(mesh: OracleMesh, cells: np.ndarray, quad: bool, params: Params) -> G
     D = np.stack([cen[rows, s1] - c0[:, None, :], cen[rows, s2] - c0[:, None, :]], axis=-2)  # (N, M, 2, 2)
     grad_op = np.linalg.pinv(D, rcond=params.rcond)                    # (N, M, 2, 2)
     members = np.stack([slot_cells[rows, s1], slot_cells[rows, s2]], axis=-1)
+    flips = np.array([[mesh.slot_flips(c, j) for j in range(M + 1)] for c in cells], dtype=np.int8).reshape(N, M + 1, 2)
+    member_flip = np.stack([flips[rows, s1], flips[rows, s2]], axis=2)          # (N, M, 2, 2)
 
     # b_jk: P^1_j(x_G) = W0 + dG . (grad_op (W_S - W0))
     dG = xG - c0[:, None, :]
@@ -192,7 +195,8 @@ def _group(mesh: OracleMesh, cells: np.ndarray, quad: bool, params: Params) -> G
         eta_opt = eta
         gamma = gamma_raw
     gamma = flush_rounding_weights(gamma)
-    return GroupTables(cells=cells, M=M, G=G, area=mesh.area[cells], members=members, grad_op=grad_op,
+    return GroupTables(cells=cells, M=M, G=G, area=mesh.area[cells], members=members, member_flip=member_flip,
+                       grad_op=grad_op,
                        dG=dG, gamma=gamma, gamma_raw=gamma_raw, eta=eta_opt, eta_raw=eta, B=B,
                        slot_cells=slot_cells, E=E, A=A)
 

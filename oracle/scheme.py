@@ -6,7 +6,8 @@ L(W)_i = -(1/|Omega_i|) sum_p |l_p| sum_k omega_k F(x_pk) . n_p with
 omega_1 = omega_2 = 1/2 (Eq. 5).  Each face flux uses the Gauss-point values
 of the two cells on its sides; at an outflow boundary face both states are
 the inner cell's value (reading: ghost = copy of the cell, so HLLC returns the
-physical flux of the inner state).
+physical flux of the inner state); at a reflective wall the outer state is the
+inner one with its normal momentum reversed.
 
 Non-physical states (rho <= 0, p <= 0 or not finite at a Gauss point) raise
 NonPhysicalState; the paper has no positivity limiter.
@@ -59,6 +60,14 @@ class OracleSolver:
         gR = np.where(self.boundary[:, None], self.gL, self.gR)
         WL = Wg[:, self.fL[:, None], self.gL]               # (nv, Nf, 2)
         WR = Wg[:, R[:, None], gR]
+        if self.nv == 4 and m.face_wall.any():
+            # reflective wall: the outer state is the inner one with its normal momentum reversed
+            n = m.face_normal[:, :, None]                    # (Nf, 2, 1)
+            mn = WL[1] * n[:, 0] + WL[2] * n[:, 1]
+            w = m.face_wall[:, None]
+            WR = WR.copy()
+            WR[1] = np.where(w, WL[1] - 2.0 * mn * n[:, 0], WR[1])
+            WR[2] = np.where(w, WL[2] - 2.0 * mn * n[:, 1], WR[2])
         self._check(WL)
         self._check(WR)
         nx = m.face_normal[:, 0][:, None]

@@ -2,6 +2,9 @@
 
 Test infrastructure only (see oracle/__init__.py).
 
+Mirror images across reflective walls carry the mirrored cell's average with
+the momentum component normal to the wall reversed.
+
 For one cell type group, with state W of shape (nv, n_cells):
 
 1. dW of the two non-centre members of each candidate, g_j = grad_op_j dW,
@@ -21,7 +24,8 @@ In linear mode R(x_G) = sum_j gamma_j P^1_j(x_G).
 Characteristic variables (Euler, Section 4): for the Gauss points of local
 face k the normal flux Jacobian n_x dF/dW + n_y dG/dW is taken at the Roe
 average of the cell averages of the cell and its neighbour across face k
-(reading: the cell itself at an outflow boundary face); its right eigenvector
+(reading: the cell itself at an outflow boundary face, its mirror image with
+the normal momentum reversed at a wall); its right eigenvector
 matrix R diagonalises it, the stencil averages are projected, U = R^-1 W,
 steps 1-5 run on each component of U, and W(x_G) = R U(x_G).
 """
@@ -86,13 +90,17 @@ def roe_eigenvectors(Wl, Wr, nx, ny, gamma):
 def _face_frames(t, W, mesh, gamma, k):
     """R and R^-1 of local face k of every cell of the group: (N, 4, 4) each."""
     nb = np.array([mesh.neighbour(int(c), k)[0] for c in t.cells])
+    wall = np.array([mesh.face_wall[mesh.cell_face[int(c)][k]] for c in t.cells])
+    side = np.array([mesh.face_side[mesh.cell_face[int(c)][k]] for c in t.cells])
     nb = np.where(nb < 0, t.cells, nb)
     p = np.array([mesh.nodes[mesh.cells[c][k]] for c in t.cells])
     q = np.array([mesh.nodes[mesh.cells[c][(k + 1) % len(mesh.cells[c])]] for c in t.cells])
     d = q - p
     ln = np.hypot(d[:, 0], d[:, 1])
     nx, ny = d[:, 1] / ln, -d[:, 0] / ln                            # outward unit normal
-    R = roe_eigenvectors(W[:, t.cells], W[:, nb], nx, ny, gamma)
+    # across a wall the neighbour is the cell's mirror image, momentum reversed across the wall
+    Wn = mesh.reflect_momentum(W[:, nb], wall & (side < 2), wall & (side >= 2))
+    R = roe_eigenvectors(W[:, t.cells], Wn, nx, ny, gamma)
     return R, np.linalg.inv(R)
 
 
@@ -101,6 +109,9 @@ def gauss_values_group(t, W: np.ndarray, params, mesh=None) -> np.ndarray:
     Characteristic reconstruction needs the mesh (neighbours and face normals)."""
     W0 = W[:, t.cells]                                              # (nv, N)
     Wm = W[:, t.members]                                            # (nv, N, M, 2)
+    if W.shape[0] == 4 and t.member_flip.any():                     # mirror images across walls
+        Wm[1] = np.where(t.member_flip[..., 0], -Wm[1], Wm[1])
+        Wm[2] = np.where(t.member_flip[..., 1], -Wm[2], Wm[2])
     if not getattr(params, "characteristic", False):
         return _weno_points(t, W0, Wm, params, np.arange(t.G))
     assert W.shape[0] == 4 and mesh is not None

@@ -32,6 +32,8 @@ class MeshInput:
     cell_ptr   (n_cells + 1,) int64 offsets into cell_nodes
     cell_nodes int64 node ids, 3 or 4 per cell, counter-clockwise
     bc         "periodic" (both directions, period = extent) or "outflow"
+    walls      outflow meshes: box sides that are reflective walls instead of outflow
+               (0: x = origin_x, 1: x = origin_x + extent_x, 2: y = origin_y, 3: y = origin_y + extent_y)
     """
     nodes: np.ndarray
     cell_ptr: np.ndarray
@@ -42,6 +44,7 @@ class MeshInput:
     name: str = ""
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    walls: tuple = ()
 
     @property
     def n_cells(self) -> int:
