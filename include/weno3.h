@@ -66,8 +66,15 @@ typedef enum { WENO_FP64 = 0, WENO_FP32C = 1 } weno_precision;
 /* Boundary description of one mesh instance. */
 typedef struct {
   int32_t bc;        /* weno_bc_kind: periodic in x and y, or outflow on every boundary face */
-  double origin[2];  /* periodic box origin (ignored for outflow)                            */
-  double extent[2];  /* periodic box size = the periods (ignored for outflow)                */
+  double origin[2];  /* box origin: periodic box, or the sides named by `walls`              */
+  double extent[2];  /* box size: the periods, or the sides named by `walls`                 */
+  int32_t walls;     /* outflow meshes, Euler: bit s set = box side s is a reflective wall
+                        (0: x = origin[0], 1: x = origin[0] + extent[0], 2: y = origin[1],
+                        3: y = origin[1] + extent[1]); a boundary face with both ends on such
+                        a side sees, outside, the inner state with its normal momentum
+                        reversed, and the mirror images across it in the stencils (Sections
+                        3.1, 3.2) carry the mirrored cell's average with that momentum
+                        component reversed.  0 = every boundary face is outflow.            */
 } weno_mesh_opts;
 
 /* Scheme parameters (defaults: weno_params_default). */

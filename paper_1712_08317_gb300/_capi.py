@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "WENO_OK", -1: "WENO_EINVAL", -2: "WENO_EMESH", -3: "WENO_EPE
 
 
 class weno_mesh_opts(C.Structure):
-    _fields_ = [("bc", C.c_int32), ("origin", C.c_double * 2), ("extent", C.c_double * 2)]
+    _fields_ = [("bc", C.c_int32), ("origin", C.c_double * 2), ("extent", C.c_double * 2), ("walls", C.c_int32)]
 
 
 class weno_params(C.Structure):

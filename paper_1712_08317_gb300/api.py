@@ -22,7 +22,8 @@ def _ptr(a: np.ndarray):
 class Mesh:
     """Host mesh (topology, renumbering, stencils) owned by the library."""
 
-    def __init__(self, nodes, cell_ptr, cell_nodes, bc="periodic", origin=(0.0, 0.0), extent=(1.0, 1.0), _handle=None):
+    def __init__(self, nodes, cell_ptr, cell_nodes, bc="periodic", origin=(0.0, 0.0), extent=(1.0, 1.0), walls=(),
+                 _handle=None):
         self._lib = capi.load()
         if _handle is not None:
             self._h = _handle
@@ -34,6 +35,7 @@ class Mesh:
             opts.bc = capi.WENO_BC_PERIODIC if bc == "periodic" else capi.WENO_BC_OUTFLOW
             opts.origin[0], opts.origin[1] = origin
             opts.extent[0], opts.extent[1] = extent
+            opts.walls = sum(1 << int(w) for w in set(walls))
             h = C.c_void_p()
             capi.check(self._lib.weno_mesh_create(_ptr(nodes), nodes.shape[0], _ptr(cell_ptr), _ptr(cell_nodes),
                                                   cell_ptr.shape[0] - 1, C.byref(opts), C.byref(h)))
@@ -46,7 +48,7 @@ class Mesh:
 
     @classmethod
     def from_input(cls, mi):
-        return cls(mi.nodes, mi.cell_ptr, mi.cell_nodes, mi.bc, mi.origin, mi.extent)
+        return cls(mi.nodes, mi.cell_ptr, mi.cell_nodes, mi.bc, mi.origin, mi.extent, getattr(mi, "walls", ()))
 
     @classmethod
     def concat(cls, meshes):

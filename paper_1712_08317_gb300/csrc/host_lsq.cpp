@@ -250,7 +250,7 @@ void cell_tables(const Mesh& m, const LsqParams& p, int64_t c, GroupTables& T, i
     double D[4] = {s0 * avg[a][0], s0 * avg[a][1], s0 * avg[b][0], s0 * avg[b][1]};  // centroid offsets
     pinv_jacobi(D, 2, 2, p.rcond, gop[j]);
     for (int e = 0; e < 4; ++e) T.gop[(j * 4 + e) * N + q] = gop[j][e];
-    T.slot[j * N + q] = slot_value_cell(m, c, j + 1);
+    T.slot[j * N + q] = slot_value_cell(m, c, j + 1) | slot_flip_bits(m, c, j + 1);
   }
   const double* v = &m.verts[c * 8];
   const int nv0 = m.nvert[c];

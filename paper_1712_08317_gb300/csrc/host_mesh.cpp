@@ -80,6 +80,18 @@ int32_t slot_value_cell(const Mesh& m, int64_t c, int j) {
   return m.slots[c * kMaxSlots + resolve_slot(m, c, j)].cell;
 }
 
+int32_t slot_flip_bits(const Mesh& m, int64_t c, int j) {
+  const Slot& s = m.slots[c * kMaxSlots + resolve_slot(m, c, j)];
+  if (s.kind != SLOT_GHOST) return 0;
+  int32_t bits = 0;
+  for (int r = 0; r < s.nref; ++r) {
+    const int8_t w = m.fwall[s.ref[r]];
+    if (w == 0) bits ^= kFlipX;
+    else if (w == 1) bits ^= kFlipY;
+  }
+  return bits;
+}
+
 int slot_polygon(const Mesh& m, int64_t c, int j, double out[4][2]) {
   const Slot& s = m.slots[c * kMaxSlots + resolve_slot(m, c, j)];
   const int64_t x = s.cell;
@@ -136,8 +148,12 @@ bool same_member(const Slot& a, const Slot& b) {
 }  // namespace
 
 int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const int64_t* cell_nodes,
-               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], Mesh& out,
+               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], int32_t walls, Mesh& out,
                std::string& err) {
+  if (walls && (bc != WENO_BC_OUTFLOW || (walls & ~15) || !(extent[0] > 0.0 && extent[1] > 0.0))) {
+    err = "walls name sides (bits 0-3) of an outflow box with positive extent";
+    return WENO_EINVAL;
+  }
   if (n_cells <= 0 || n_nodes <= 0) { err = "empty mesh"; return WENO_EINVAL; }
   if (n_cells > (int64_t)INT32_MAX / 8) { err = "too many cells for 32-bit indices"; return WENO_EINVAL; }
   if (bc == WENO_BC_PERIODIC && !(extent[0] > 0.0 && extent[1] > 0.0)) {
@@ -353,6 +369,18 @@ int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const
       m.fny.push_back(-dx / L);
       m.flen.push_back(L);
       m.cell_face[i * 4 + k] = f;
+      int8_t wall = -1;
+      if (x < 0 && walls) {
+        // a wall face lies, with both ends, on a side of the box named in `walls`
+        const double tol = 1e-9 * std::max(extent[0], extent[1]);
+        for (int side = 0; side < 4; ++side) {
+          const int axis = side / 2;
+          const double line = origin[axis] + (side % 2 ? extent[axis] : 0.0);
+          if ((walls >> side & 1) && std::fabs(v[2 * k + axis] - line) <= tol && std::fabs(v[2 * k1 + axis] - line) <= tol)
+            wall = (int8_t)axis;
+        }
+      }
+      m.fwall.push_back(wall);
       if (x >= 0) m.cell_face[(int64_t)x * 4 + m.nb_face[i * 4 + k]] = f;
       else m.n_boundary++;
     }
@@ -451,6 +479,7 @@ int concat_meshes(const Mesh* const* meshes, int32_t n, Mesh& out, std::string& 
       m.fnx.push_back(a.fnx[f]);
       m.fny.push_back(a.fny[f]);
       m.flen.push_back(a.flen[f]);
+      m.fwall.push_back(a.fwall[f]);
     }
     for (int k = 0; k < a.n_inst; ++k) {
       m.inst_period.push_back(a.inst_period[2 * k]);

@@ -53,6 +53,7 @@ struct Mesh {
   std::vector<int32_t> fL, fR;       // fR = -1: outflow boundary face
   std::vector<int8_t> fkL, fkR;
   std::vector<double> fnx, fny, flen;
+  std::vector<int8_t> fwall;         // reflective wall faces: 0 on an x side, 1 on a y side; -1 otherwise
 
   int64_t n() const { return nQ + nT; }
   bool is_quad(int64_t c) const { return c < nQ; }
@@ -61,7 +62,7 @@ struct Mesh {
 // Builds topology, renumbering, faces and stencils.  Returns a weno_status
 // code and fills err on failure.
 int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const int64_t* cell_nodes,
-               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], Mesh& out,
+               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], int32_t walls, Mesh& out,
                std::string& err);
 
 // Disjoint union (batched instances).
@@ -79,5 +80,10 @@ int slot_polygon(const Mesh& m, int64_t c, int j, double out[4][2]);
 
 // Cell whose average slot j reads at run time (a mirror image reads the cell it mirrors).
 int32_t slot_value_cell(const Mesh& m, int64_t c, int j);
+
+// Momentum components reversed in the value of slot j (mirror images across reflective walls):
+// kFlipX | kFlipY bits, to be or-ed into the cell id of the device stencil table.
+constexpr int32_t kFlipX = 1 << 30, kFlipY = 1 << 29, kSlotCell = (1 << 29) - 1;
+int32_t slot_flip_bits(const Mesh& m, int64_t c, int j);
 
 }  // namespace weno

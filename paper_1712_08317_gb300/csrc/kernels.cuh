@@ -35,6 +35,71 @@ template <> struct Sub<9> {
 
 template <typename T> __device__ __forceinline__ T fabs_(T x) { return x < T(0) ? -x : x; }
 
+// Vector loads / stores of one cell's NV values.
+template <typename T, int NV>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, T w[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) w[v] = __ldg(p + v);
+}
+template <>
+__device__ __forceinline__ void load_vec<float, 4>(const float* __restrict__ p, float w[4]) {
+  const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+  w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+}
+template <>
+__device__ __forceinline__ void load_vec<double, 4>(const double* __restrict__ p, double w[4]) {
+  const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 y = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  w[0] = x.x; w[1] = x.y; w[2] = y.x; w[3] = y.y;
+}
+template <typename T, int NV>
+__device__ __forceinline__ void store_vec(T* p, const T w[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) p[v] = w[v];
+}
+template <>
+__device__ __forceinline__ void store_vec<float, 4>(float* p, const float w[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
+}
+template <>
+__device__ __forceinline__ void store_vec<double, 4>(double* p, const double w[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(w[0], w[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(w[2], w[3]);
+}
+
+// Stencil table entries: cell id in the low 29 bits; on meshes with reflective walls
+// bit 30 / bit 29 mark a mirror image whose x / y momentum is reversed.
+constexpr int32_t kDevFlipX = 1 << 30, kDevFlipY = 1 << 29, kDevSlotCell = (1 << 29) - 1;
+
+// Flip mask of variable v (Euler: rho u -> bit 30, rho v -> bit 29).
+template <bool WALLS, int NV>
+__device__ __forceinline__ int32_t flip_mask(int v) {
+  return (WALLS && NV == 4) ? (v == 1 ? kDevFlipX : (v == 2 ? kDevFlipY : 0)) : 0;
+}
+
+// Value of variable v of stencil entry `raw` (hi and, compensated, lo), momentum reversed for
+// mirror images across walls.
+template <typename T, int NV, bool WALLS, bool COMP>
+__device__ __forceinline__ T slot_delta(const T* __restrict__ U, const T* __restrict__ Ulo, int32_t raw, int v,
+                                        int32_t fm, T w0, T l0) {
+  const int64_t cs = WALLS ? (raw & kDevSlotCell) : raw;
+  T a = __ldg(U + cs * NV + v);
+  T b = COMP ? __ldg(Ulo + cs * NV + v) : T(0);
+  if (WALLS && (raw & fm)) { a = -a; b = -b; }
+  return COMP ? (a - w0) + (b - l0) : a - w0;
+}
+
+// All variables of stencil entry `raw` (hi only), momentum reversed across walls.
+template <typename T, bool WALLS>
+__device__ __forceinline__ void slot_state4(const T* __restrict__ U, int32_t raw, T w[4]) {
+  const int64_t cs = WALLS ? (raw & kDevSlotCell) : raw;
+  load_vec<T, 4>(U + cs * 4, w);
+  if (WALLS) {
+    if (raw & kDevFlipX) w[1] = -w[1];
+    if (raw & kDevFlipY) w[2] = -w[2];
+  }
+}
+
 // Error-free sum (Knuth TwoSum): s + e = a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -66,7 +131,7 @@ __device__ __forceinline__ df df_mul(df a, df b) {
 
 // ---------------------------------------------------------------- K1
 // Threads t in [0, N*NV): cell q = t / NV of the group, variable v = t % NV.
-template <typename T, int NV, int M, int G, bool COMP>
+template <typename T, int NV, int M, int G, bool COMP, bool WALLS>
 __global__ void __launch_bounds__(256) k_reconstruct(
     const T* __restrict__ U, const T* __restrict__ Ulo, const int32_t* __restrict__ slot,
     const T* __restrict__ gop, const T* __restrict__ dg, const T* __restrict__ gam,
@@ -82,13 +147,10 @@ __global__ void __launch_bounds__(256) k_reconstruct(
     // differences to the stencil cells (slots 1..M), replacements already resolved
     T dW[M + 1];
     dW[0] = T(0);
+    const int32_t fm = flip_mask<WALLS, NV>(v);
 #pragma unroll
-    for (int s = 1; s <= M; ++s) {
-      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
-      T d = __ldg(U + cs * NV + v) - w0;
-      if (COMP) d += __ldg(Ulo + cs * NV + v) - l0;
-      dW[s] = d;
-    }
+    for (int s = 1; s <= M; ++s)
+      dW[s] = slot_delta<T, NV, WALLS, COMP>(U, Ulo, __ldg(slot + (int64_t)(s - 1) * N + q), v, fm, w0, l0);
     // candidate gradients g_j = D_j^+ (dW_a, dW_b), beta_j = |Omega| |g_j|^2
     T gx[M], gy[M], beta[M];
     const T a0 = __ldg(area + c);
@@ -217,7 +279,7 @@ __device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const fl
 
 // Candidate gradients and smoothness indicators of one (cell, variable), as
 // candidate pairs (the padding candidate of odd M has g = 0, beta = 0).
-template <int NV, int M>
+template <int NV, int M, bool WALLS>
 __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, const float* __restrict__ Ulo,
                                                const int32_t* __restrict__ slot, int64_t slot_pitch,
                                                const float4* __restrict__ gop4, int64_t pitch, int64_t q, int64_t c,
@@ -227,11 +289,10 @@ __device__ __forceinline__ void cell_gradients(const float* __restrict__ U, cons
   l0 = __ldg(Ulo + c * NV + v);
   float dW[M + 1];
   dW[0] = 0.0f;
+  const int32_t fm = flip_mask<WALLS, NV>(v);
 #pragma unroll
-  for (int s = 1; s <= M; ++s) {
-    const int64_t cs = __ldg(slot + (int64_t)(s - 1) * slot_pitch + q);
-    dW[s] = (__ldg(U + cs * NV + v) - w0) + (__ldg(Ulo + cs * NV + v) - l0);
-  }
+  for (int s = 1; s <= M; ++s)
+    dW[s] = slot_delta<float, NV, WALLS, true>(U, Ulo, __ldg(slot + (int64_t)(s - 1) * slot_pitch + q), v, fm, w0, l0);
   float gx[2 * ((M + 1) / 2)], gy[2 * ((M + 1) / 2)], b[2 * ((M + 1) / 2)];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -269,7 +330,7 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
     const int64_t c = first + q;
     float w0, l0;
     CandPairs<P> cp;
-    cell_gradients<NV, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
+    cell_gradients<NV, M, false>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
     float* out = Wg + (gbase + q * G) * NV + v;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
@@ -367,7 +428,7 @@ struct TmaTile {
   static constexpr int SMEM = NSTAGE * STAGE + 16;             // stages + two mbarriers
 };
 
-template <int M, int G>
+template <int M, int G, bool WALLS>
 __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WENO_K1_TILE) k_reconstruct_tma(
     const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
     const __grid_constant__ CUtensorMap map_g1, const float* __restrict__ U, const float* __restrict__ Ulo,
@@ -412,7 +473,7 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
     CandPairs<P> cp;
     if (q < N) {
       const int64_t c = first + q;
-      cell_gradients<4, M>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
+      cell_gradients<4, M, WALLS>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
     }
     const bool ok = mbar_wait_bounded(&bar[st], phase[st]);
     phase[st] ^= 1u;
@@ -544,36 +605,6 @@ __device__ __forceinline__ void hllc(const T wl[4], const T wr[4], T nx, T ny, T
   out[3] = f[3];
 }
 
-template <typename T, int NV>
-__device__ __forceinline__ void load_vec(const T* __restrict__ p, T w[NV]) {
-#pragma unroll
-  for (int v = 0; v < NV; ++v) w[v] = __ldg(p + v);
-}
-template <>
-__device__ __forceinline__ void load_vec<float, 4>(const float* __restrict__ p, float w[4]) {
-  const float4 x = __ldg(reinterpret_cast<const float4*>(p));
-  w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
-}
-template <>
-__device__ __forceinline__ void load_vec<double, 4>(const double* __restrict__ p, double w[4]) {
-  const double2 x = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 y = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  w[0] = x.x; w[1] = x.y; w[2] = y.x; w[3] = y.y;
-}
-template <typename T, int NV>
-__device__ __forceinline__ void store_vec(T* p, const T w[NV]) {
-#pragma unroll
-  for (int v = 0; v < NV; ++v) p[v] = w[v];
-}
-template <>
-__device__ __forceinline__ void store_vec<float, 4>(float* p, const float w[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
-}
-template <>
-__device__ __forceinline__ void store_vec<double, 4>(double* p, const double w[4]) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(w[0], w[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(w[2], w[3]);
-}
 
 // flag[instance] is set when a Gauss-point state of a face of that instance is
 // non-physical; nQ and inst map the left Gauss-value index back to its cell's
@@ -600,6 +631,11 @@ __global__ void __launch_bounds__(256) k_face(
       else {
 #pragma unroll
         for (int v = 0; v < NV; ++v) wr[v] = wl[v];
+        if (NV == 4 && ir == -2) {  // reflective wall: normal momentum reversed
+          const T mn = wl[1] * nx + wl[2] * ny;
+          wr[1] = wl[1] - T(2) * mn * nx;
+          wr[2] = wl[2] - T(2) * mn * ny;
+        }
       }
       if (NV == 4) {
         hllc<T>(wl, wr, nx, ny, prm.gas_gamma, fk, bad);
@@ -673,7 +709,7 @@ __device__ __forceinline__ void roe_rows(const T Wl[4], const T Wr[4], T nx, T n
   }
 }
 
-template <typename T, int M, int G, bool COMP>
+template <typename T, int M, int G, bool COMP, bool WALLS>
 __global__ void __launch_bounds__(256) k_reconstruct_char(
     const T* __restrict__ U, const T* __restrict__ Ulo, const int32_t* __restrict__ slot,
     const T* __restrict__ gop, const T* __restrict__ dg, const T* __restrict__ gam,
@@ -694,19 +730,16 @@ __global__ void __launch_bounds__(256) k_reconstruct_char(
     const T l0 = COMP ? __ldg(Ulo + c * 4 + l) : T(0);
     T dW[M + 1];
     dW[0] = T(0);
+    const int32_t fm = flip_mask<WALLS, 4>(l);
 #pragma unroll
-    for (int s = 1; s <= M; ++s) {
-      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
-      T d = __ldg(U + cs * 4 + l) - w0;
-      if (COMP) d += __ldg(Ulo + cs * 4 + l) - l0;
-      dW[s] = d;
-    }
+    for (int s = 1; s <= M; ++s)
+      dW[s] = slot_delta<T, 4, WALLS, COMP>(U, Ulo, __ldg(slot + (int64_t)(s - 1) * N + q), l, fm, w0, l0);
     const T a0 = __ldg(area + c);
 #pragma unroll 1
     for (int k = 0; k < G / 2; ++k) {
       // face frame: Roe average with the neighbour, outward normal from the face's two Gauss points
       T Wn[4];
-      load_vec<T, 4>(U + (int64_t)__ldg(slot + (int64_t)k * N + q) * 4, Wn);  // slot k+1: across face k
+      slot_state4<T, WALLS>(U, __ldg(slot + (int64_t)k * N + q), Wn);  // slot k+1: across face k
       const T x0 = __ldg(dg + (int64_t)(4 * k) * N + q), y0 = __ldg(dg + (int64_t)(4 * k + 1) * N + q);
       const T x1 = __ldg(dg + (int64_t)(4 * k + 2) * N + q), y1 = __ldg(dg + (int64_t)(4 * k + 3) * N + q);
       const T tx = x1 - x0, ty = y1 - y0, it = T(1) / sqrt(tx * tx + ty * ty);
@@ -794,7 +827,7 @@ struct CharTile {
   static constexpr int SMEM = STAGE + 16;                      // one buffer + one mbarrier (padded)
 };
 
-template <int M, int G>
+template <int M, int G, bool WALLS>
 __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 / WENO_K1_TILE)
     k_reconstruct_char_tma(const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
                            const __grid_constant__ CUtensorMap map_g1, const __grid_constant__ CUtensorMap map_gop,
@@ -840,11 +873,10 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
     const float w0 = W0[l], l0 = __ldg(Ulo + c * 4 + l);
     float dW[M + 1];
     dW[0] = 0.f;
+    const int32_t fm = flip_mask<WALLS, 4>(l);
 #pragma unroll
-    for (int s = 1; s <= M; ++s) {
-      const int64_t cs = __ldg(slot + (int64_t)(s - 1) * N + q);
-      dW[s] = (__ldg(U + cs * 4 + l) - w0) + (__ldg(Ulo + cs * 4 + l) - l0);
-    }
+    for (int s = 1; s <= M; ++s)
+      dW[s] = slot_delta<float, 4, WALLS, true>(U, Ulo, __ldg(slot + (int64_t)(s - 1) * N + q), l, fm, w0, l0);
     const float a0 = __ldg(area + c);
     const bool ok = mbar_wait_bounded(&bar[0], phase);
     phase ^= 1u;
@@ -855,7 +887,7 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
 #pragma unroll 1
     for (int k = 0; k < G / 2; ++k) {
       float Wn[4];
-      load_vec<float, 4>(U + (int64_t)__ldg(slot + (int64_t)k * N + q) * 4, Wn);  // slot k+1: across face k
+      slot_state4<float, WALLS>(U, __ldg(slot + (int64_t)k * N + q), Wn);  // slot k+1: across face k
       const float4 d0 = sds[(2 * k) * L::TILE + cl], d1 = sds[(2 * k + 1) * L::TILE + cl];
       const float tx = d1.x - d0.x, ty = d1.y - d0.y, it = rsqrtf(tx * tx + ty * ty);
       float Lr[4], Rr[4];

@@ -106,6 +106,7 @@ struct weno_solver_s {
   double *dt_dev = nullptr, *red = nullptr, *cell_dt = nullptr;
   int* flag = nullptr;
   int debug_stall = 0;  // weno_solver_debug_stall
+  bool walls = false;   // the mesh has reflective wall faces (stencil values carry momentum flips)
   std::vector<void*> allocs;
   Launch k1q, k1t, k2, k3q, k3t;
   cudaStream_t cap = nullptr;
@@ -141,12 +142,15 @@ struct weno_solver_s {
 namespace {
 
 using S = weno_solver_s;
+static_assert(weno::dev::kDevFlipX == weno::kFlipX && weno::dev::kDevFlipY == weno::kFlipY &&
+                  weno::dev::kDevSlotCell == weno::kSlotCell,
+              "stencil table bit layout shared by the host tables and the kernels");
 
 // ------------------------------------------------------------ launches
 // Cell reconstruction into the Gauss-value array wg.  which: bit 0 = quad group,
 // bit 1 = triangle group.
-template <typename T, int NV, bool COMP>
-void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which) {
+template <typename T, int NV, bool COMP, bool WALLS>
+void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which) {
   const T* u = static_cast<const T*>(U);
   const T* ul = static_cast<const T*>(Ulo);
   const T eps = (T)s.prm.eps, th = (T)s.prm.theta;
@@ -157,20 +161,20 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
         using CQ = weno::dev::CharTile<12, 8>;
         using CT = weno::dev::CharTile<9, 6>;
         if (s.nQ && (which & 1))
-          weno::dev::k_reconstruct_char_tma<12, 8><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
+          weno::dev::k_reconstruct_char_tma<12, 8, WALLS><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
               s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
               (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
         if (s.nT && (which & 2))
-          weno::dev::k_reconstruct_char_tma<9, 6><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
+          weno::dev::k_reconstruct_char_tma<9, 6, WALLS><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
               s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
               8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
       } else {
         if (s.nQ && (which & 1))
-          weno::dev::k_reconstruct_char<T, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
+          weno::dev::k_reconstruct_char<T, 12, 8, COMP, WALLS><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
               u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0,
               0, (T*)wg, eps, th, gg, s.prm.linear);
         if (s.nT && (which & 2))
-          weno::dev::k_reconstruct_char<T, 9, 6, COMP><<<grid_of(s.k1t, s.nT * 4), s.k1t.block, 0, st>>>(
+          weno::dev::k_reconstruct_char<T, 9, 6, COMP, WALLS><<<grid_of(s.k1t, s.nT * 4), s.k1t.block, 0, st>>>(
               u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT,
               s.nQ, 8 * s.nQ, (T*)wg, eps, th, gg, s.prm.linear);
       }
@@ -182,11 +186,11 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
       using TQ = weno::dev::TmaTile<12, 8>;
       using TT = weno::dev::TmaTile<9, 6>;
       if (s.nQ && (which & 1))
-        weno::dev::k_reconstruct_tma<12, 8><<<tma_grid(s.k1q, s.nQ), TQ::THREADS, TQ::SMEM, st>>>(
+        weno::dev::k_reconstruct_tma<12, 8, WALLS><<<tma_grid(s.k1q, s.nQ), TQ::THREADS, TQ::SMEM, st>>>(
             s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
             s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       if (s.nT && (which & 2))
-        weno::dev::k_reconstruct_tma<9, 6><<<tma_grid(s.k1t, s.nT), TT::THREADS, TT::SMEM, st>>>(
+        weno::dev::k_reconstruct_tma<9, 6, WALLS><<<tma_grid(s.k1t, s.nT), TT::THREADS, TT::SMEM, st>>>(
             s.t_map_gpm, s.t_map_dgs, s.t_map_g1, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
             s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       return;
@@ -204,14 +208,24 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
           s.prm.linear);
   } else {
     if (s.nQ && (which & 1))
-      weno::dev::k_reconstruct<T, NV, 12, 8, COMP><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
+      weno::dev::k_reconstruct<T, NV, 12, 8, COMP, WALLS><<<grid_of(s.k1q, s.nQ * NV), s.k1q.block, 0, st>>>(
           u, ul, s.q_slot, (const T*)s.q_gop, (const T*)s.q_dg, (const T*)s.q_gam, (const T*)s.area, s.nQ, 0, 0,
           (T*)wg, eps, th, s.prm.linear);
     if (s.nT && (which & 2))
-      weno::dev::k_reconstruct<T, NV, 9, 6, COMP><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
+      weno::dev::k_reconstruct<T, NV, 9, 6, COMP, WALLS><<<grid_of(s.k1t, s.nT * NV), s.k1t.block, 0, st>>>(
           u, ul, s.t_slot, (const T*)s.t_gop, (const T*)s.t_dg, (const T*)s.t_gam, (const T*)s.area, s.nT, s.nQ,
           8 * s.nQ, (T*)wg, eps, th, s.prm.linear);
   }
+}
+
+// Walls only change the stencil gathers (momentum flips of mirror images); meshes without
+// walls run kernels without that code.
+template <typename T, int NV, bool COMP>
+void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which) {
+  if constexpr (NV == 4) {
+    if (s.walls) return launch_reconstruct_impl<T, NV, COMP, true>(s, U, Ulo, wg, st, which);
+  }
+  launch_reconstruct_impl<T, NV, COMP, false>(s, U, Ulo, wg, st, which);
 }
 
 template <typename T, int NV, bool COMP>
@@ -425,18 +439,24 @@ int setup_tma(S& s) {
     if ((r = make_map_2d(enc, &s.t_map_dgs, s.t_dg, 4 * s.t_pitch, 6, 16 * s.t_pitch, 4 * kTile, 6))) return r;
     if ((r = make_map_2d(enc, &s.t_map_g1, s.t_gam1, 2 * s.t_pitch, 6, 8 * s.t_pitch, 2 * kTile, 6))) return r;
   }
-  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TQ::SMEM));
-  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM));
+  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          TQ::SMEM));
+  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          TT::SMEM));
+  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          TQ::SMEM));
+  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          TT::SMEM));
   if (s.prm.characteristic) {
     // D_j^+ rows: M float4 rows
     if (s.nQ && (r = make_map_2d(enc, &s.q_map_gop, s.q_gop, 4 * s.q_pitch, 12, 16 * s.q_pitch, 4 * kTile, 12)))
       return r;
     if (s.nT && (r = make_map_2d(enc, &s.t_map_gop, s.t_gop, 4 * s.t_pitch, 9, 16 * s.t_pitch, 4 * kTile, 9)))
       return r;
-    CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_char_tma<12, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            weno::dev::CharTile<12, 8>::SMEM));
-    CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_char_tma<9, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            weno::dev::CharTile<9, 6>::SMEM));
+    for (auto fn : {weno::dev::k_reconstruct_char_tma<12, 8, false>, weno::dev::k_reconstruct_char_tma<12, 8, true>})
+      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::CharTile<12, 8>::SMEM));
+    for (auto fn : {weno::dev::k_reconstruct_char_tma<9, 6, false>, weno::dev::k_reconstruct_char_tma<9, 6, true>})
+      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::CharTile<9, 6>::SMEM));
   }
   s.tma = true;
   return WENO_OK;
@@ -476,7 +496,7 @@ int weno_mesh_create(const double* node_xy, int64_t n_nodes, const int64_t* cell
     auto m = std::make_unique<weno_mesh_s>();
     std::string err;
     int r = weno::build_mesh(node_xy, n_nodes, cell_ptr, cell_nodes, n_cells, opts->bc, opts->origin, opts->extent,
-                             m->m, err);
+                             opts->walls, m->m, err);
     if (r) return fail(r, err);
     *out = m.release();
   } catch (const std::bad_alloc&) {
@@ -586,7 +606,7 @@ int weno_mesh_cell_tables(weno_mesh_t mesh, const weno_params* params, int64_t c
   mg[0] = T.M;
   mg[1] = T.G;
   for (int j = 0; j < T.M; ++j) {
-    slot_cells[j] = T.slot[(size_t)j * N + q];
+    slot_cells[j] = T.slot[(size_t)j * N + q] & weno::kSlotCell;
     for (int e = 0; e < 4; ++e) grad_op[j * 4 + e] = T.gop[(size_t)(j * 4 + e) * N + q];
   }
   for (int g = 0; g < T.G; ++g) {
@@ -609,6 +629,8 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
     return fail(WENO_EINVAL, "parameters out of range (eps > 0, theta >= 1, gamma > 1)");
   if (p.characteristic && p.eqn != WENO_EQN_EULER)
     return fail(WENO_EINVAL, "characteristic variables are defined for the Euler equations only");
+  const bool walls = std::any_of(mesh->m.fwall.begin(), mesh->m.fwall.end(), [](int8_t w) { return w >= 0; });
+  if (walls && p.eqn != WENO_EQN_EULER) return fail(WENO_EINVAL, "reflective walls are defined for the Euler equations only");
   const Mesh& m = mesh->m;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::unique_ptr<S> s;
@@ -620,6 +642,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   CK(cudaGetDevice(&s->dev));
   CK(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
   s->prm = p;
+  s->walls = walls;
   if (!(s->prm.rcond > 0)) s->prm.rcond = 1e-12;
   s->nv = p.eqn == WENO_EQN_EULER ? 4 : 1;
   s->fp64 = p.precision == WENO_FP64;
@@ -700,7 +723,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
     auto gbase = [&](int64_t c) -> int64_t { return c < d.nQ ? 8 * c : 8 * d.nQ + 6 * (c - d.nQ); };
     for (int64_t f = 0; f < d.nF; ++f) {
       gl[f] = (int32_t)(gbase(m.fL[f]) + 2 * m.fkL[f]);
-      gr[f] = m.fR[f] >= 0 ? (int32_t)(gbase(m.fR[f]) + 2 * m.fkR[f]) : -1;
+      gr[f] = m.fR[f] >= 0 ? (int32_t)(gbase(m.fR[f]) + 2 * m.fkR[f]) : (m.fwall[f] >= 0 ? -2 : -1);
     }
     if ((r = upload(d, &d.gl, gl, st))) return r;
     if ((r = upload(d, &d.gr, gr, st))) return r;

@@ -21,7 +21,15 @@ CASES = {
     "euler-mixed": dict(cfg=2, kind="mixed", n=30, eqn="euler", init=S.density_wave),
     "riemann-outflow": dict(cfg=3, kind="mixed", n=30, eqn="euler", init=None),
     "vortex-lowq": dict(cfg=5, kind=None, n=36, eqn="euler", init=S.isentropic_vortex),
+    # reflective walls on the x = 1 and y = 0 sides (corner at (1, 0)), flow towards both
+    "walls-mixed": dict(cfg=3, kind="mixed", n=26, eqn="euler", init="walls", walls=(1, 2)),
 }
+
+
+def _walls_flow(x, y, t=0.0):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x) * np.cos(np.pi * y)
+    u, v, p = 0.5 + 0 * x, -0.4 + 0 * x, 1.0 + 0.1 * np.cos(2 * np.pi * y)
+    return np.stack([rho, rho * u, rho * v, p / 0.4 + 0.5 * rho * (u * u + v * v)])
 
 # FP64 bound: states, max over cells of |W_gpu - W_oracle|_inf / |W_oracle|_inf (per-cell relative);
 # residuals, max over cells of |R_gpu - R_oracle| / max_cells |R_oracle| per variable
@@ -34,8 +42,11 @@ def _case(name):
         mi = S.stretched_vortex_mesh(c["n"], seed=7)
     else:
         mi = S.mesh_for_config(c["cfg"], n=c["n"], seed=7, kind=c["kind"])
+    mi.walls = c.get("walls", ())
     if c["init"] is None:
         W = S.four_quadrant_average(mi, seed=7)
+    elif c["init"] == "walls":
+        W = S.cell_average(mi, _walls_flow)
     else:
         W = S.cell_average(mi, c["init"])
     return mi, W, c["eqn"]
@@ -99,7 +110,8 @@ def test_linear_scheme_matches_oracle(name):
     assert _rel(sol.to_host(sol.residual(U)), ref) < TOL_FP64
 
 
-@pytest.mark.parametrize("name", ["euler-mixed", "vortex-lowq", "riemann-outflow", "scalar-quad", "euler-tri"])
+@pytest.mark.parametrize("name", ["euler-mixed", "vortex-lowq", "riemann-outflow", "scalar-quad", "euler-tri",
+                                  "walls-mixed"])
 def test_fp32c_tracks_the_oracle(name):
     """FP32 reconstruction / weights / flux with a compensated state: FP32-level agreement."""
     mi, W, osol = _oracle(name)
@@ -279,7 +291,7 @@ def test_characteristic_fp64_residual_and_steps_match_oracle(name):
     assert _rel_cell(sol.to_host(U), ref) < TOL_FP64
 
 
-@pytest.mark.parametrize("name", ["euler-mixed", "riemann-outflow", "vortex-lowq"])
+@pytest.mark.parametrize("name", ["euler-mixed", "riemann-outflow", "vortex-lowq", "walls-mixed"])
 def test_characteristic_fp32c_tracks_the_oracle(name):
     mi, W, osol = _oracle(name, characteristic=True)
     sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c", characteristic=True)

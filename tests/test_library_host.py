@@ -127,3 +127,17 @@ def test_clockwise_cells_are_reoriented():
     m2 = Mesh(mi.nodes, mi.cell_ptr, cn, mi.bc, mi.origin, mi.extent)
     assert np.array_equal(m1.perm, m2.perm)
     assert np.array_equal(m1.weight_stats()[1], m2.weight_stats()[1])
+
+
+def test_wall_options_are_validated(lib):
+    """Reflective walls name sides of an outflow box (bits 0-3); anything else is rejected."""
+    from paper_1712_08317_gb300 import _capi
+    from paper_1712_08317_gb300.api import Mesh
+    mi = S.mesh_for_config(3, n=6, seed=1, kind="mixed")
+    m = Mesh(mi.nodes, mi.cell_ptr, mi.cell_nodes, "outflow", (0.0, 0.0), (1.0, 1.0), walls=(0, 3))
+    assert m.n_cells == mi.n_cells
+    for bc, walls, extent in (("periodic", (1,), (1.0, 1.0)), ("outflow", (4,), (1.0, 1.0)),
+                              ("outflow", (1,), (0.0, 1.0))):
+        with pytest.raises(_capi.WenoError) as e:
+            Mesh(mi.nodes, mi.cell_ptr, mi.cell_nodes, bc, (0.0, 0.0), extent, walls=walls)
+        assert e.value.code == _capi.WENO_EINVAL
