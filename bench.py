@@ -319,6 +319,67 @@ def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic
     return row
 
 
+TUBES = {  # (rho, u, p) left | right, split at x = 0.5, final time
+    "sod": ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.2),
+    "lax": ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 0.14),
+}
+
+
+def _strip_mesh(nx, ny=4):
+    """Cartesian nx x ny quads on [0, 1] x [0, ny/nx]: outflow ends, reflective top and bottom walls."""
+    import synthetic as S
+    X = np.linspace(0.0, 1.0, nx + 1)
+    Y = np.linspace(0.0, ny / nx, ny + 1)
+    xx, yy = np.meshgrid(X, Y, indexing="xy")
+    nodes = np.stack([xx.ravel(), yy.ravel()], 1)
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    a = (i + (nx + 1) * j).ravel()
+    q = np.stack([a, a + 1, a + 1 + (nx + 1), a + (nx + 1)], 1)
+    return S.MeshInput(nodes, np.arange(0, 4 * len(q) + 1, 4), q.ravel(), "outflow", (0.0, 0.0),
+                       (1.0, ny / nx), name=f"strip-{nx}", walls=(2, 3))
+
+
+def run_tubes(args):
+    """Sod and Lax shock tubes through the CUDA path: L1(rho) against the exact Riemann solution."""
+    import torch
+    import synthetic as S
+    from paper_1712_08317_gb300.api import Mesh, Solver
+    out = {}
+    for name, (left, right, T) in TUBES.items():
+        f = S.shock_tube(left, right)
+        rows = []
+        for nx in [int(x) for x in args.ladder_tube.split(",")]:
+            mi = _strip_mesh(nx)
+            mesh = Mesh.from_input(mi)
+            W0 = S.cell_average(mi, f, order=3)
+            ex = S.cell_average(mi, lambda x, y: f(x, y, T), order=3)
+            area = _cell_areas(mi)
+            row = {"nx": nx, "cells": mi.n_cells}
+            for prec in args.precisions.split(","):
+                for ch in (False, True):
+                    sol = Solver(mesh, eqn="euler", precision=prec, characteristic=ch)
+                    U, Ul = sol.to_device(W0)
+                    t, steps = 0.0, 0
+                    while t < T - 1e-12:
+                        dt = min(float(sol.max_dt(U, Ul, args.cfl)[0]), T - t)
+                        sol.step(U, Ul, dt)
+                        t += dt
+                        steps += 1
+                    torch.cuda.synchronize()
+                    key = prec + ("-char" if ch else "")
+                    try:
+                        sol.check()
+                    except Exception as exc:
+                        row[key] = {"steps": steps, "failed": str(exc).split(":")[0]}
+                        continue
+                    e = np.abs(sol.to_host(U, Ul)[0] - ex[0])
+                    row[key] = {"steps": steps, "l1": float((e * area).sum() / area.sum())}
+            rows.append(row)
+            print(json.dumps({"tube": name, **row}), flush=True)
+        out[name] = rows
+    print(json.dumps({"tubes": out, "cfl": args.cfl}), flush=True)
+
+
 def run_accuracy(args):
     """Convergence ladders to t = 2 through the CUDA path: FP64 and FP32C, L1 / Linf of rho vs exact."""
     ladders = {"densitywave-tri": [int(x) for x in args.ladder_dw.split(",")],
@@ -368,6 +429,8 @@ def parse_args(argv=None):
     ap.add_argument("--precisions", default="fp64,fp32c")
     ap.add_argument("--characteristic", action="store_true", help="accuracy mode: characteristic-variable reconstruction")
     ap.add_argument("--raw-weights", action="store_true", help="accuracy mode: linear weights without the optimisation")
+    ap.add_argument("--tubes", action="store_true", help="Sod and Lax shock tubes (walls top and bottom) vs exact")
+    ap.add_argument("--ladder-tube", default="100,200,400")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     return ap.parse_args(argv)
 
@@ -379,6 +442,9 @@ def main():
         return
     if args.accuracy:
         run_accuracy(args)
+        return
+    if args.tubes:
+        run_tubes(args)
         return
     assert args.warmup >= 3, "at least 3 warm-up steps"
     import torch

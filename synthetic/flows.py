@@ -13,7 +13,8 @@ import math
 
 import numpy as np
 
-__all__ = ["scalar_wave", "density_wave", "isentropic_vortex", "four_quadrant_states",
+__all__ = ["scalar_wave", "density_wave", "isentropic_vortex", "four_quadrant_states", "riemann_exact",
+           "shock_tube",
            "cell_average", "four_quadrant_average", "euler_prim_to_cons"]
 
 GAMMA = 1.4
@@ -78,6 +79,76 @@ def four_quadrant_average(mesh, seed: int, gamma=GAMMA, order=5):
         return euler_prim_to_cons(s[..., 0], s[..., 1], s[..., 2], s[..., 3], gamma)
 
     return cell_average(mesh, f, order)
+
+
+def riemann_exact(left, right, xi, gamma=GAMMA):
+    """Exact solution of the 1D Riemann problem for an ideal gas (the classical construction with
+    a pressure function for each side, Newton iteration for the star pressure and sampling of
+    the self-similar fan), as primitive (rho, u, p) at the similarity coordinates xi = x / t."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    al, ar = np.sqrt(gamma * pl / rl), np.sqrt(gamma * pr / rr)
+    g1, g2 = (gamma - 1) / (2 * gamma), (gamma + 1) / (2 * gamma)
+
+    def side(p, r, pk, ak):  # f_K(p) and its derivative
+        if p > pk:  # shock
+            A, B = 2 / ((gamma + 1) * r), (gamma - 1) / (gamma + 1) * pk
+            q = np.sqrt(A / (p + B))
+            return (p - pk) * q, q * (1 - 0.5 * (p - pk) / (p + B))
+        f = 2 * ak / (gamma - 1) * ((p / pk) ** g1 - 1)  # rarefaction
+        return f, (p / pk) ** (-g2) / (r * ak)
+
+    p = max(1e-8, 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (al + ar))
+    for _ in range(100):
+        fl, dl = side(p, rl, pl, al)
+        fr, dr = side(p, rr, pr, ar)
+        dp = (fl + fr + ur - ul) / (dl + dr)
+        p = max(1e-10, p - dp)
+        if abs(dp) < 1e-14 * p:
+            break
+    fl, _ = side(p, rl, pl, al)
+    fr, _ = side(p, rr, pr, ar)
+    us = 0.5 * (ul + ur) + 0.5 * (fr - fl)
+    xi = np.asarray(xi, dtype=np.float64)
+    out = np.empty((3,) + xi.shape)
+    for k, s in np.ndenumerate(xi):
+        if s <= us:  # left of the contact
+            r, u, pk, ak, sgn = rl, ul, pl, al, 1.0
+        else:
+            r, u, pk, ak, sgn = rr, ur, pr, ar, -1.0
+        if p > pk:  # shock on this side
+            rs = r * (p / pk + (gamma - 1) / (gamma + 1)) / ((gamma - 1) / (gamma + 1) * p / pk + 1)
+            S = u - sgn * ak * np.sqrt(g2 * p / pk + g1)
+            inside = (s >= S) if sgn > 0 else (s <= S)
+            val = (rs, us, p) if inside else (r, u, pk)
+        else:  # rarefaction: head, tail, fan between
+            as_ = ak * (p / pk) ** g1
+            head, tail = u - sgn * ak, us - sgn * as_
+            if (sgn > 0 and s <= head) or (sgn < 0 and s >= head):
+                val = (r, u, pk)
+            elif (sgn > 0 and s >= tail) or (sgn < 0 and s <= tail):
+                val = (r * (p / pk) ** (1 / gamma), us, p)
+            else:
+                c = 2 / (gamma + 1) + sgn * (gamma - 1) / ((gamma + 1) * ak) * (u - s)
+                val = (r * c ** (2 / (gamma - 1)), 2 / (gamma + 1) * (sgn * ak + (gamma - 1) / 2 * u + s),
+                       pk * c ** (2 * gamma / (gamma - 1)))
+        out[(slice(None),) + k] = val
+    return out
+
+
+def shock_tube(left, right, x0=0.5, gamma=GAMMA):
+    """f(x, y, t): conservative state of the exact 1D Riemann solution split at x = x0."""
+    def f(x, y, t=0.0):
+        x = np.asarray(x, dtype=np.float64)
+        if t <= 0.0:
+            lo = np.array(left)[:, None] * np.ones(x.size)
+            hi = np.array(right)[:, None] * np.ones(x.size)
+            prim = np.where((x.ravel() < x0)[None], lo, hi).reshape((3,) + x.shape)
+        else:
+            prim = riemann_exact(left, right, (x - x0) / t, gamma)
+        rho, u, p = prim
+        return euler_prim_to_cons(rho, u, 0 * u, p, gamma)
+    return f
 
 
 def _gauss_legendre01(order: int):

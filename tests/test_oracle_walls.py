@@ -128,3 +128,16 @@ def test_mirror_images_reverse_the_normal_momentum():
     cen = mesh0.centroid[t0.cells]
     edge = (cen[:, 0] > 0.9) & (cen[:, 1] > 0.3) & (cen[:, 1] < 0.7)
     assert np.abs(got0[1] - lin(xG[..., 0], xG[..., 1])[1])[edge].max() > 1e-3
+
+
+def test_exact_riemann_solver_reproduces_the_textbook_star_states():
+    """The reference solution used for the shock tubes (synthetic.riemann_exact): Sod's problem
+    (1, 0, 1 | 0.125, 0, 0.1) has p* = 0.30313, u* = 0.92745, rho*L = 0.42632, rho*R = 0.26557
+    (Toro, Riemann Solvers and Numerical Methods for Fluid Dynamics, ch. 4, test 1); a state
+    and its mirror image give u* = 0 exactly."""
+    rho, u, p = S.riemann_exact((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), np.array([0.2, 1.5]))
+    assert abs(p[0] - 0.30313) < 5e-6 and abs(u[0] - 0.92745) < 5e-6
+    assert abs(rho[0] - 0.42632) < 5e-6 and abs(rho[1] - 0.26557) < 5e-6
+    ps, rho_s, speed = _wall_shock_exact(1.0, 1.0, 1.0)
+    r2, u2, p2 = S.riemann_exact((1.0, 1.0, 1.0), (1.0, -1.0, 1.0), np.array([speed + 1e-9, -1e-9]))
+    assert abs(u2[0]) < 1e-12 and abs(p2[0] / ps - 1) < 1e-12 and abs(r2[0] / rho_s - 1) < 1e-12
