@@ -319,64 +319,102 @@ def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic
     return row
 
 
-TUBES = {  # (rho, u, p) left | right, split at x = 0.5, final time
+TUBES = {  # (rho, u, p) left | right, split at x = 0.5, final time (the paper's Sod and Lax set-ups)
     "sod": ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.2),
-    "lax": ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 0.14),
+    "lax": ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 0.16),
 }
 
 
-def _strip_mesh(nx, ny=4):
-    """Cartesian nx x ny quads on [0, 1] x [0, ny/nx]: outflow ends, reflective top and bottom walls."""
+def _shu_osher(x, y, t=0.0):
+    """Shu-Osher initial data: a Mach 3 shock at x = 1 running into a density wave."""
     import synthetic as S
-    X = np.linspace(0.0, 1.0, nx + 1)
-    Y = np.linspace(0.0, ny / nx, ny + 1)
-    xx, yy = np.meshgrid(X, Y, indexing="xy")
-    nodes = np.stack([xx.ravel(), yy.ravel()], 1)
-    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
-    a = (i + (nx + 1) * j).ravel()
-    q = np.stack([a, a + 1, a + 1 + (nx + 1), a + (nx + 1)], 1)
-    return S.MeshInput(nodes, np.arange(0, 4 * len(q) + 1, 4), q.ravel(), "outflow", (0.0, 0.0),
-                       (1.0, ny / nx), name=f"strip-{nx}", walls=(2, 3))
+    left = x <= 1.0
+    rho = np.where(left, 3.857134, 1.0 + 0.2 * np.sin(5.0 * x))
+    u = np.where(left, 2.629369, 0.0)
+    p = np.where(left, 10.33333, 1.0)
+    return S.euler_prim_to_cons(rho, u, 0.0 * u, p)
+
+
+def _march(sol, U, Ul, T, cfl):
+    t, steps = 0.0, 0
+    while t < T - 1e-12:
+        dt = min(float(sol.max_dt(U, Ul, cfl)[0]), T - t)
+        sol.step(U, Ul, dt)
+        t += dt
+        steps += 1
+    return steps
 
 
 def run_tubes(args):
-    """Sod and Lax shock tubes through the CUDA path: L1(rho) against the exact Riemann solution."""
+    """The paper's shock-tube problems through the CUDA path.  Sod (t = 0.2) and Lax (t = 0.16) on
+    [0,1] x [0,0.5], outflow (non-reflecting) on every side, regular and irregular quad and
+    triangle meshes: L1(rho) against the exact Riemann solution.  Shu-Osher (t = 1.8) on
+    [0,10] x [0,0.25], h = 1/40, reflective walls in y: L1(rho) against a reference run with
+    h = 1/320 on a Cartesian strip."""
     import torch
     import synthetic as S
     from paper_1712_08317_gb300.api import Mesh, Solver
+    variants = [(p, ch) for p in args.precisions.split(",") for ch in (False, True)]
+
+    def run(mi, W0, T, ex):
+        mesh = Mesh.from_input(mi)
+        area = _cell_areas(mi)
+        row = {"cells": mi.n_cells}
+        for prec, ch in variants:
+            sol = Solver(mesh, eqn="euler", precision=prec, characteristic=ch)
+            U, Ul = sol.to_device(W0)
+            steps = _march(sol, U, Ul, T, args.cfl)
+            torch.cuda.synchronize()
+            key = prec + ("-char" if ch else "")
+            try:
+                sol.check()
+            except Exception as exc:
+                row[key] = {"steps": steps, "failed": str(exc).split(":")[0]}
+                continue
+            W = sol.to_host(U, Ul)
+            e = np.abs(W[0] - ex(mi, W))
+            row[key] = {"steps": steps, "l1": float((e * area).sum() / area.sum())}
+        return row
+
     out = {}
     for name, (left, right, T) in TUBES.items():
         f = S.shock_tube(left, right)
         rows = []
-        for nx in [int(x) for x in args.ladder_tube.split(",")]:
-            mi = _strip_mesh(nx)
-            mesh = Mesh.from_input(mi)
-            W0 = S.cell_average(mi, f, order=3)
-            ex = S.cell_average(mi, lambda x, y: f(x, y, T), order=3)
-            area = _cell_areas(mi)
-            row = {"nx": nx, "cells": mi.n_cells}
-            for prec in args.precisions.split(","):
-                for ch in (False, True):
-                    sol = Solver(mesh, eqn="euler", precision=prec, characteristic=ch)
-                    U, Ul = sol.to_device(W0)
-                    t, steps = 0.0, 0
-                    while t < T - 1e-12:
-                        dt = min(float(sol.max_dt(U, Ul, args.cfl)[0]), T - t)
-                        sol.step(U, Ul, dt)
-                        t += dt
-                        steps += 1
-                    torch.cuda.synchronize()
-                    key = prec + ("-char" if ch else "")
-                    try:
-                        sol.check()
-                    except Exception as exc:
-                        row[key] = {"steps": steps, "failed": str(exc).split(":")[0]}
-                        continue
-                    e = np.abs(sol.to_host(U, Ul)[0] - ex[0])
-                    row[key] = {"steps": steps, "l1": float((e * area).sum() / area.sum())}
-            rows.append(row)
-            print(json.dumps({"tube": name, **row}), flush=True)
+        for kind in ("quad", "tri"):
+            for delta, label in ((0.0, "regular"), (0.1, "irregular")):
+                for nx in [int(x) for x in args.ladder_tube.split(",")]:
+                    mi = S.tube_mesh(nx, nx // 2, (1.0, 0.5), kind, delta, seed=1)
+                    W0 = S.cell_average(mi, f, order=3)
+                    exact = S.cell_average(mi, lambda x, y: f(x, y, T), order=3)[0]
+                    row = {"mesh": f"{label} {kind}", "h": 1.0 / nx,
+                           **run(mi, W0, T, lambda m, W: exact)}
+                    rows.append(row)
+                    print(json.dumps({"tube": name, **row}), flush=True)
         out[name] = rows
+    # Shu-Osher: reference on a fine Cartesian strip (FP64)
+    T = 1.8
+    ref_mi = S.tube_mesh(3200, 2, (10.0, 2 * 10.0 / 3200), "quad", 0.0, seed=0, walls=(2, 3))
+    ref_sol = Solver(Mesh.from_input(ref_mi), eqn="euler", precision="fp64")
+    V, _ = ref_sol.to_device(S.cell_average(ref_mi, _shu_osher, order=3))
+    _march(ref_sol, V, None, T, args.cfl)
+    Wref = ref_sol.to_host(V)
+    cx = np.array(ref_mi.nodes[ref_mi.padded_cells()[0]].mean(axis=1)[:, 0])
+    o = np.argsort(cx)
+    xr, rr = cx[o][::2], Wref[0][o][::2]  # two cells per column: average them
+    rr = 0.5 * (Wref[0][o][::2] + Wref[0][o][1::2])
+
+    def shu_ref(m, W):
+        cen = m.nodes[m.padded_cells()[0]].mean(axis=1)[:, 0]
+        return np.interp(cen, xr, rr)
+
+    rows = []
+    for kind in ("quad", "tri"):
+        mi = S.tube_mesh(400, 10, (10.0, 0.25), kind, 0.1, seed=2, walls=(2, 3))
+        row = {"mesh": f"irregular {kind}", "h": 1.0 / 40, **run(mi, S.cell_average(mi, _shu_osher, order=3), T,
+                                                                   shu_ref)}
+        rows.append(row)
+        print(json.dumps({"tube": "shu-osher", **row}), flush=True)
+    out["shu-osher"] = rows
     print(json.dumps({"tubes": out, "cfl": args.cfl}), flush=True)
 
 
@@ -430,7 +468,7 @@ def parse_args(argv=None):
     ap.add_argument("--characteristic", action="store_true", help="accuracy mode: characteristic-variable reconstruction")
     ap.add_argument("--raw-weights", action="store_true", help="accuracy mode: linear weights without the optimisation")
     ap.add_argument("--tubes", action="store_true", help="Sod and Lax shock tubes (walls top and bottom) vs exact")
-    ap.add_argument("--ladder-tube", default="100,200,400")
+    ap.add_argument("--ladder-tube", default="100,200")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     return ap.parse_args(argv)
 

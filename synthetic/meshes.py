@@ -17,7 +17,7 @@ import math
 import numpy as np
 
 __all__ = ["MeshInput", "quad_grid", "perturbed_quads", "split_quads", "stretched_vortex_mesh",
-           "mesh_for_config", "batch_instances"]
+           "mesh_for_config", "batch_instances", "tube_mesh"]
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -74,13 +74,14 @@ def _grid_coords(n: int, x0: float, L: float, mapping=None) -> np.ndarray:
     return x0 + s
 
 
-def quad_grid(n: int, origin=(0.0, 0.0), extent=(1.0, 1.0), xmap=None, ymap=None):
-    """Tensor grid of n x n quads.  Node (i, j) has id i + (n+1) j; cells CCW."""
+def quad_grid(n: int, origin=(0.0, 0.0), extent=(1.0, 1.0), xmap=None, ymap=None, ny=None):
+    """Tensor grid of n x ny quads (ny = n by default).  Node (i, j) has id i + (n+1) j; cells CCW."""
+    ny = n if ny is None else ny
     X = _grid_coords(n, origin[0], extent[0], xmap)
-    Y = _grid_coords(n, origin[1], extent[1], ymap)
+    Y = _grid_coords(ny, origin[1], extent[1], ymap)
     xx, yy = np.meshgrid(X, Y, indexing="xy")
     nodes = np.stack([xx.ravel(), yy.ravel()], axis=1)
-    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    i, j = np.meshgrid(np.arange(n), np.arange(ny), indexing="xy")
     i = i.ravel()
     j = j.ravel()
     a = i + (n + 1) * j
@@ -106,7 +107,7 @@ def _quads_convex(pos: np.ndarray, quads: np.ndarray, min_cross: np.ndarray) -> 
 
 
 def perturbed_quads(n: int, origin=(0.0, 0.0), extent=(1.0, 1.0), delta=0.1, seed=0,
-                    xmap=None, ymap=None):
+                    xmap=None, ymap=None, ny=None):
     """Quad grid whose interior nodes move i.i.d. uniformly in [-delta h, delta h]^2.
 
     h is the local minimum grid spacing in each direction.  Boundary nodes stay
@@ -115,14 +116,15 @@ def perturbed_quads(n: int, origin=(0.0, 0.0), extent=(1.0, 1.0), delta=0.1, see
     undisplaced cell area (a sliver, or a non-convex quad) has its interior
     nodes redrawn until no such quad is left.
     """
-    nodes, quads, X, Y = quad_grid(n, origin, extent, xmap, ymap)
+    ny = n if ny is None else ny
+    nodes, quads, X, Y = quad_grid(n, origin, extent, xmap, ymap, ny)
     rng = _rng(seed)
     ax = delta * _local_spacing(X)
     ay = delta * _local_spacing(Y)
     AX, AY = np.meshgrid(ax, ay, indexing="xy")
     amp = np.stack([AX.ravel(), AY.ravel()], axis=1)
-    ii, jj = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy")
-    interior = ((ii > 0) & (ii < n) & (jj > 0) & (jj < n)).ravel()
+    ii, jj = np.meshgrid(np.arange(n + 1), np.arange(ny + 1), indexing="xy")
+    interior = ((ii > 0) & (ii < n) & (jj > 0) & (jj < ny)).ravel()
     amp[~interior] = 0.0
     disp = rng.uniform(-1.0, 1.0, size=nodes.shape) * amp
     pos = nodes + disp
@@ -204,6 +206,17 @@ def _vortex_maps(L: float, a: float = 9.0 / 11.0):
         return g(s + phi) - g(np.asarray(phi))
 
     return g, gy
+
+
+def tube_mesh(nx: int, ny: int, extent, kind="quad", delta=0.1, seed=0, walls=()):
+    """Outflow box [0, Lx] x [0, Ly] of nx x ny perturbed quads (kind "quad"), all split into
+    triangles ("tri") or 30 % split ("mixed"); `walls` names reflective sides (see MeshInput)."""
+    frac = {"quad": 0.0, "tri": 1.0, "mixed": 0.3}[kind]
+    pos, quads = perturbed_quads(nx, (0.0, 0.0), tuple(extent), delta, seed, ny=ny)
+    mi = _assemble(pos, quads, frac, seed, "outflow", (0.0, 0.0), tuple(extent), f"tube-{kind}-{nx}x{ny}",
+                   {"nx": nx, "ny": ny, "split": frac, "delta": delta})
+    mi.walls = tuple(walls)
+    return mi
 
 
 def stretched_vortex_mesh(n: int, frac=0.3, delta=0.4, seed=0, L=10.0):
