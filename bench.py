@@ -418,6 +418,60 @@ def run_tubes(args):
     print(json.dumps({"tubes": out, "cfl": args.cfl}), flush=True)
 
 
+def run_shock_vortex(args):
+    """The shock-vortex interaction of the paper's tests through the CUDA path: [0,2] x [0,1],
+    stationary Mach 1.1 shock at x = 0.5, vortex at (0.25, 0.5), reflective top and bottom
+    walls, outflow (zero-gradient) left and right, t = 0.8, h = 1/100 on irregular quad and
+    triangle meshes.  No exact solution: reports completion, extrema, the FP32C-FP64 L1
+    difference and the density on the centre line."""
+    import torch
+    import synthetic as S
+    from paper_1712_08317_gb300.api import Mesh, Solver
+    T = 0.8
+    out = []
+    for kind in ("quad", "tri"):
+        mi = S.tube_mesh(200, 100, (2.0, 1.0), kind, 0.1, seed=4, walls=(2, 3))
+        mesh = Mesh.from_input(mi)
+        W0 = S.cell_average(mi, S.shock_vortex, order=4)
+        area = _cell_areas(mi)
+        cen = mi.nodes[mi.padded_cells()[0]].mean(axis=1)
+        line = np.abs(cen[:, 1] - 0.5) < 0.006
+        order = np.argsort(cen[line, 0])
+        row = {"mesh": f"irregular {kind}", "cells": mi.n_cells}
+        for ch in (False, True):
+            res = {}
+            for prec in args.precisions.split(","):
+                sol = Solver(mesh, eqn="euler", precision=prec, characteristic=ch)
+                U, Ul = sol.to_device(W0)
+                t0 = time.perf_counter()
+                steps = _march(sol, U, Ul, T, args.cfl)
+                torch.cuda.synchronize()
+                try:
+                    sol.check()
+                except Exception as exc:
+                    res[prec] = {"steps": steps, "failed": str(exc).split(":")[0]}
+                    continue
+                W = sol.to_host(U, Ul)
+                p = 0.4 * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
+                res[prec] = {"steps": steps, "seconds": time.perf_counter() - t0, "rho_min": float(W[0].min()),
+                             "rho_max": float(W[0].max()), "p_min": float(p.min()), "W": W}
+            if "W" in res.get("fp64", {}) and "W" in res.get("fp32c", {}):
+                d = np.abs(res["fp32c"]["W"][0] - res["fp64"]["W"][0])
+                res["l1_rho_fp32c_vs_fp64"] = float((d * area).sum() / area.sum())
+            if "W" in res.get("fp64", {}):
+                rl = res["fp64"]["W"][0][line][order]
+                xl = cen[line, 0][order]
+                res["centre_line_rho_fp64"] = {f"{x:.2f}": float(np.interp(x, xl, rl)) for x in
+                                               (0.25, 0.5, 0.75, 1.0, 1.25, 1.5)}
+            for v in res.values():
+                if isinstance(v, dict):
+                    v.pop("W", None)
+            row["characteristic" if ch else "componentwise"] = res
+        out.append(row)
+        print(json.dumps({"shock_vortex": row}), flush=True)
+    print(json.dumps({"shock_vortex": out, "t": T, "cfl": args.cfl}), flush=True)
+
+
 def run_accuracy(args):
     """Convergence ladders to t = 2 through the CUDA path: FP64 and FP32C, L1 / Linf of rho vs exact."""
     ladders = {"densitywave-tri": [int(x) for x in args.ladder_dw.split(",")],
@@ -469,6 +523,7 @@ def parse_args(argv=None):
     ap.add_argument("--raw-weights", action="store_true", help="accuracy mode: linear weights without the optimisation")
     ap.add_argument("--tubes", action="store_true", help="Sod and Lax shock tubes (walls top and bottom) vs exact")
     ap.add_argument("--ladder-tube", default="100,200")
+    ap.add_argument("--shock-vortex", action="store_true", help="shock-vortex interaction (walls top and bottom)")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     return ap.parse_args(argv)
 
@@ -483,6 +538,9 @@ def main():
         return
     if args.tubes:
         run_tubes(args)
+        return
+    if args.shock_vortex:
+        run_shock_vortex(args)
         return
     assert args.warmup >= 3, "at least 3 warm-up steps"
     import torch

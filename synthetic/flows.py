@@ -14,7 +14,7 @@ import math
 import numpy as np
 
 __all__ = ["scalar_wave", "density_wave", "isentropic_vortex", "four_quadrant_states", "riemann_exact",
-           "shock_tube",
+           "shock_tube", "shock_vortex",
            "cell_average", "four_quadrant_average", "euler_prim_to_cons"]
 
 GAMMA = 1.4
@@ -149,6 +149,33 @@ def shock_tube(left, right, x0=0.5, gamma=GAMMA):
         rho, u, p = prim
         return euler_prim_to_cons(rho, u, 0 * u, p, gamma)
     return f
+
+
+def shock_vortex(x, y, t=0.0, mach=1.1, x_shock=0.5, center=(0.25, 0.5), kappa=0.3, mu=0.204, rc=0.05,
+                 gamma=GAMMA):
+    """Initial data of the shock-vortex interaction: a stationary normal shock of Mach number
+    `mach` at x = x_shock with the upstream state rho = 1, u = mach sqrt(gamma), v = 0, p = 1 and the
+    downstream state from the normal-shock relations; upstream, an isentropic vortex perturbs the
+    velocity by kappa eta e^{mu (1 - eta^2)} (sin theta, -cos theta) and the temperature p / rho by
+    -(gamma - 1) kappa^2 / (4 mu gamma) e^{2 mu (1 - eta^2)}, eta = r / rc (t is not used)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    m2 = mach * mach
+    u1 = mach * np.sqrt(gamma)
+    r21 = (gamma + 1) * m2 / ((gamma - 1) * m2 + 2)          # density ratio across the shock
+    p21 = 1 + 2 * gamma / (gamma + 1) * (m2 - 1)             # pressure ratio
+    dx, dy = x - center[0], y - center[1]
+    eta = np.sqrt(dx * dx + dy * dy) / rc
+    th = np.arctan2(dy, dx)
+    e = np.exp(mu * (1 - eta * eta))
+    T = 1.0 - (gamma - 1) * kappa ** 2 / (4 * mu * gamma) * e * e
+    rho_up = T ** (1.0 / (gamma - 1))                          # isentropic: p / rho^gamma = 1
+    up = x < x_shock
+    rho = np.where(up, rho_up, r21)
+    u = np.where(up, u1 + kappa * eta * e * np.sin(th), u1 / r21)
+    v = np.where(up, -kappa * eta * e * np.cos(th), 0.0)
+    p = np.where(up, rho_up * T, p21)
+    return euler_prim_to_cons(rho, u, v, p, gamma)
 
 
 def _gauss_legendre01(order: int):
