@@ -1,13 +1,22 @@
 // sm_103a kernels of the WENO3 residual and the SSP-RK3 stage update.
 //
-//   k_reconstruct  one thread per (cell, variable): candidate gradients from
-//                  gathered stencil averages, smoothness indicators, split
-//                  linear weights, new indicator, nonlinear weights and the
-//                  Gauss-point values (Sections 3.1-3.4).
+//   K1 (reconstruction, Sections 3.1-3.4): candidate gradients from gathered
+//                  stencil averages, smoothness indicators, split linear weights,
+//                  new indicator, nonlinear weights and the Gauss-point values;
+//                  one thread per (cell, variable):
+//     k_reconstruct_tma       FP32C Euler, tables staged in shared memory by TMA
+//     k_reconstruct_f32c      FP32C scalar advection
+//     k_reconstruct           FP64
+//     k_reconstruct_char_tma  FP32C Euler, characteristic variables (four lanes
+//                             per cell exchange variables by shuffles)
+//     k_reconstruct_char      FP64, characteristic variables
 //   k_face         one thread per face: two Gauss points, rotated HLLC
-//                  (Euler) or upwind (scalar) flux, |l|/2 (F1 + F2) (Eqs. 5-6).
+//                  (Euler) or upwind (scalar) flux, |l|/2 (F1 + F2) (Eqs. 5-6);
+//                  at reflective walls the outer state is the inner one mirrored.
 //   k_gather       one thread per cell: signed gather of its face fluxes
 //                  (Eq. 4, no atomics) fused with the RK3 stage (Section 4).
+// The reconstruction kernels take WALLS = true on meshes with reflective walls:
+// stencil entries then carry momentum flips for mirror images.
 //
 // Layouts: state U[cell][v] (cell-major), Gauss values Wg[point][v] with the
 // points of a quad at 8q..8q+7 and of a triangle at 8 nQ + 6t.., face fluxes
