@@ -185,6 +185,34 @@ def test_batched_instances_equal_standalone_runs(precision):
         off += m.n_cells
 
 
+@pytest.mark.parametrize("characteristic", [False, True])
+def test_batched_instances_with_walls_equal_standalone_runs(characteristic):
+    """Instances with and without reflective walls in one launch == separate solvers (FP32C)."""
+    a = S.mesh_for_config(3, n=11, seed=4, kind="mixed")
+    a.walls = (0, 3)
+    b = S.mesh_for_config(2, n=9, seed=5, kind="tri")
+    insts = [a, b]
+    inits = [S.cell_average(a, _walls_flow), S.cell_average(b, S.density_wave)]
+    meshes = [Mesh.from_input(m) for m in insts]
+    singles = [Solver(m, eqn="euler", precision="fp32c", characteristic=characteristic) for m in meshes]
+    states = [s.to_device(w) for s, w in zip(singles, inits)]
+    dts = [s.max_dt(U, Ul, 0.4)[0] for s, (U, Ul) in zip(singles, states)]
+    for s, (U, Ul), dt in zip(singles, states, dts):
+        for _ in range(3):
+            s.step(U, Ul, dt)
+    big = Solver(Mesh.concat(meshes), eqn="euler", precision="fp32c", characteristic=characteristic)
+    U, Ul = big.to_device(np.concatenate(inits, axis=1))
+    dt_dev = torch.tensor(dts, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        big.step_instances(U, Ul, dt_dev)
+    torch.cuda.synchronize()
+    out = big.to_host(U, Ul)
+    off = 0
+    for s, (Ui, Uli), m in zip(singles, states, insts):
+        assert np.array_equal(out[:, off:off + m.n_cells], s.to_host(Ui, Uli))
+        off += m.n_cells
+
+
 def test_nonphysical_state_is_reported_and_cleared():
     mi, W, _ = _oracle("euler-mixed")
     sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp64")
