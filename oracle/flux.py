@@ -19,7 +19,13 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["hllc_flux", "upwind_flux", "euler_normal_flux", "pressure"]
+__all__ = ["hllc_flux", "upwind_flux", "euler_normal_flux", "pressure", "primitive_to_conservative"]
+
+
+def primitive_to_conservative(q, gamma):
+    """(rho, u, v, p) -> (rho, rho u, rho v, E) with E = p / (gamma - 1) + rho (u^2 + v^2) / 2 (Eq. 2)."""
+    rho, u, v, p = (float(x) for x in q)
+    return np.array([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
 
 
 def pressure(W, gamma):

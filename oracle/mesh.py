@@ -20,6 +20,12 @@ Conventions (fixed readings, shared in writing with the CUDA library):
   mirror of i0).  A mirror image carries the average of the cell it mirrors
   (zero-gradient outflow).  Without them, corner stencils become so
   degenerate that the optimised linear weights reach |gamma| ~ 300.
+* Box sides of an outflow mesh may instead be reflective walls, over the
+  whole side or from a point along it on (the wall of the double Mach
+  reflection starts at x = 1/6), or inflow sides whose faces see a
+  prescribed outer state in the flux; the stencil images across an inflow
+  face are the outflow ones (reading: the paper states the boundary values,
+  not how the reconstruction continues across them).
 * Stencil (figures of Sections 3.1 and 3.2 are missing): the "child of face
   neighbour i_m at node v" is the cell across i_m's other face incident to v.
   Quad: i1..i4 across faces 0..3; i5, i6 = children of i1 at v0, v1;
@@ -68,7 +74,7 @@ class OracleMesh:
     """Topology + geometry + stencils of a 2D mesh of triangles and quadrilaterals."""
 
     def __init__(self, nodes, cell_ptr, cell_nodes, bc="periodic", origin=(0.0, 0.0), extent=(1.0, 1.0),
-                 walls=()):
+                 walls=(), wall_from=(0.0, 0.0, 0.0, 0.0), inflow=()):
         self.nodes = np.asarray(nodes, dtype=np.float64)
         cell_ptr = np.asarray(cell_ptr, dtype=np.int64)
         cell_nodes = np.asarray(cell_nodes, dtype=np.int64)
@@ -77,8 +83,10 @@ class OracleMesh:
         self.extent = tuple(float(v) for v in extent)
         self.n_cells = int(cell_ptr.shape[0] - 1)
         self.walls = frozenset(int(w) for w in walls)
-        if self.walls and bc == "periodic":
-            raise MeshError("walls are sides of an outflow box")
+        self.wall_from = tuple(float(v) for v in wall_from)
+        self.inflow = frozenset(int(w) for w in inflow)
+        if (self.walls or self.inflow) and bc == "periodic":
+            raise MeshError("walls and inflow sides are sides of an outflow box")
         self._orient_cells(cell_ptr, cell_nodes)
         self._node_classes()
         self._faces()
@@ -88,10 +96,12 @@ class OracleMesh:
 
     @classmethod
     def from_input(cls, m):
-        return cls(m.nodes, m.cell_ptr, m.cell_nodes, m.bc, m.origin, m.extent, getattr(m, "walls", ()))
+        return cls(m.nodes, m.cell_ptr, m.cell_nodes, m.bc, m.origin, m.extent, getattr(m, "walls", ()),
+                   getattr(m, "wall_from", (0.0, 0.0, 0.0, 0.0)), getattr(m, "inflow", ()))
 
     def _face_sides(self):
-        """Box side of every boundary face (-1 elsewhere) and whether it is a reflective wall."""
+        """Box side of every boundary face (-1 elsewhere), whether it is a reflective wall (on a wall
+        side, midpoint at least wall_from[side] along the side) and whether it is an inflow face."""
         self.face_side = np.full(self.n_faces, -1, dtype=np.int64)
         lo, ext = np.array(self.origin), np.array(self.extent)
         tol = 1e-9 * ext.max()
@@ -101,7 +111,15 @@ class OracleMesh:
             for side, (axis, val) in enumerate(((0, lo[0]), (0, lo[0] + ext[0]), (1, lo[1]), (1, lo[1] + ext[1]))):
                 if abs(a[axis] - val) <= tol and abs(b[axis] - val) <= tol and abs(m[axis] - val) <= tol:
                     self.face_side[f] = side
-        self.face_wall = np.array([s in self.walls for s in self.face_side], dtype=bool)
+        self.face_wall = np.zeros(self.n_faces, dtype=bool)
+        self.face_inflow = np.zeros(self.n_faces, dtype=bool)
+        for f in np.flatnonzero(self.face_side >= 0):
+            side = int(self.face_side[f])
+            t = 1 - side // 2                                    # axis along the side
+            a, b = self.face_line(f)
+            along = 0.5 * (a[t] + b[t]) - lo[t]
+            self.face_wall[f] = side in self.walls and along >= self.wall_from[side]
+            self.face_inflow[f] = side in self.inflow and not self.face_wall[f]
 
     def reflect_momentum(self, W, fx, fy):
         """State with its x (y) momentum reversed where fx (fy) is set (reflection across a wall parallel

@@ -57,6 +57,11 @@ class Params:
     gas_gamma: float = 1.4
     adv: tuple = (1.0, 1.0)  # advection velocity of the scalar equation
     characteristic: bool = False  # Euler: reconstruct characteristic variables (Section 4)
+    # prescribed outer state of inflow faces (Euler): primitive (rho, u, v, p) inflow_a at the
+    # Gauss points x with n . x < c0 + s t, inflow_b elsewhere; inflow_line = (n_x, n_y, c0, s)
+    inflow_a: tuple | None = None
+    inflow_b: tuple | None = None
+    inflow_line: tuple = (1.0, 0.0, 0.0, 0.0)
 
 
 @dataclass

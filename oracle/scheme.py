@@ -7,7 +7,12 @@ omega_1 = omega_2 = 1/2 (Eq. 5).  Each face flux uses the Gauss-point values
 of the two cells on its sides; at an outflow boundary face both states are
 the inner cell's value (reading: ghost = copy of the cell, so HLLC returns the
 physical flux of the inner state); at a reflective wall the outer state is the
-inner one with its normal momentum reversed.
+inner one with its normal momentum reversed; at an inflow face it is the
+prescribed state of `Params.inflow_*` at that Gauss point and time (the double
+Mach reflection imposes the exact post-shock state and, on the top side, the
+exact motion of the incident shock: a state that jumps across a moving line).
+The residual takes the time t of its stage; the RK3 stages of Section 4 sit
+at t, t + dt and t + dt/2.
 
 Non-physical states (rho <= 0, p <= 0 or not finite at a Gauss point) raise
 NonPhysicalState; the paper has no positivity limiter.
@@ -20,7 +25,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .flux import hllc_flux, upwind_flux, pressure
+from .flux import hllc_flux, upwind_flux, pressure, primitive_to_conservative
 from .mesh import OracleMesh
 from .reconstruction import Params, precompute
 from .weno import gauss_values_group
@@ -45,6 +50,18 @@ class OracleSolver:
         self.gL = np.stack([2 * m.face_kL, 2 * m.face_kL + 1], axis=1)
         self.gR = np.stack([2 * m.face_kR + 1, 2 * m.face_kR], axis=1)
         self.boundary = m.face_R < 0
+        self.inflow = None
+        if m.face_inflow.any():
+            p = self.params
+            if self.nv != 4 or p.inflow_a is None or p.inflow_b is None:
+                raise ValueError("inflow faces need the Euler equations and both prescribed states")
+            self.inflow_a = primitive_to_conservative(p.inflow_a, p.gas_gamma)
+            self.inflow_b = primitive_to_conservative(p.inflow_b, p.gas_gamma)
+            nx, ny, c0, self.inflow_speed = (float(v) for v in p.inflow_line)
+            f = np.flatnonzero(m.face_inflow)
+            xg = m.cell_gauss[self.fL[f][:, None], self.gL[f]]   # (n_in, 2 points, 2)
+            self.inflow = f
+            self.inflow_xi = nx * xg[..., 0] + ny * xg[..., 1] - c0
 
     def gauss_values(self, W: np.ndarray) -> np.ndarray:
         Wg = np.full((self.nv, self.mesh.n_cells, 8), np.nan)
@@ -52,7 +69,12 @@ class OracleSolver:
             Wg[:, t.cells, :t.G] = gauss_values_group(t, W, self.params, self.mesh)
         return Wg
 
-    def face_fluxes(self, W: np.ndarray) -> np.ndarray:
+    def inflow_states(self, t: float) -> np.ndarray:
+        """Prescribed outer states of the inflow faces at time t: (4, n_inflow, 2 Gauss points)."""
+        a = self.inflow_xi < self.inflow_speed * t
+        return np.where(a[None], self.inflow_a[:, None, None], self.inflow_b[:, None, None])
+
+    def face_fluxes(self, W: np.ndarray, t: float = 0.0) -> np.ndarray:
         """F_f = |l_f|/2 (F(x_f1) + F(x_f2)), normal pointing from L to R: (nv, n_faces)."""
         m = self.mesh
         Wg = self.gauss_values(W)
@@ -68,6 +90,9 @@ class OracleSolver:
             WR = WR.copy()
             WR[1] = np.where(w, WL[1] - 2.0 * mn * n[:, 0], WR[1])
             WR[2] = np.where(w, WL[2] - 2.0 * mn * n[:, 1], WR[2])
+        if self.inflow is not None:
+            WR = WR.copy()
+            WR[:, self.inflow] = self.inflow_states(t)
         self._check(WL)
         self._check(WR)
         nx = m.face_normal[:, 0][:, None]
@@ -85,21 +110,22 @@ class OracleSolver:
             if np.any(Wq[0] <= 0.0) or np.any(pressure(Wq, self.params.gas_gamma) <= 0.0):
                 raise NonPhysicalState("rho <= 0 or p <= 0 at a Gauss point")
 
-    def residual(self, W: np.ndarray) -> np.ndarray:
-        """L(W) of Eq. (4): (nv, n_cells)."""
-        F = self.face_fluxes(W)
+    def residual(self, W: np.ndarray, t: float = 0.0) -> np.ndarray:
+        """L(W) of Eq. (4) at time t (t only enters through inflow faces): (nv, n_cells)."""
+        F = self.face_fluxes(W, t)
         acc = np.zeros_like(W)
         np.add.at(acc, (slice(None), self.fL), -F)
         inner = ~self.boundary
         np.add.at(acc, (slice(None), self.fR[inner]), F[:, inner])
         return acc / self.mesh.area[None, :]
 
-    def rk3_step(self, W: np.ndarray, dt: float, L=None) -> np.ndarray:
-        """Third-order TVD Runge-Kutta step of Section 4."""
+    def rk3_step(self, W: np.ndarray, dt: float, L=None, t: float = 0.0) -> np.ndarray:
+        """Third-order TVD Runge-Kutta step of Section 4 from time t; its stages evaluate the
+        residual (or the operator L(w, t)) at t, t + dt and t + dt/2."""
         L = L or self.residual
-        W1 = W + dt * L(W)
-        W2 = 0.75 * W + 0.25 * W1 + 0.25 * dt * L(W1)
-        return W / 3.0 + 2.0 / 3.0 * W2 + 2.0 / 3.0 * dt * L(W2)
+        W1 = W + dt * L(W, t)
+        W2 = 0.75 * W + 0.25 * W1 + 0.25 * dt * L(W1, t + 1.0 * dt)
+        return W / 3.0 + 2.0 / 3.0 * W2 + 2.0 / 3.0 * dt * L(W2, t + 0.5 * dt)
 
     def max_dt(self, W: np.ndarray, cfl: float) -> float:
         m = self.mesh
@@ -125,10 +151,13 @@ class OracleSolver:
         return (W * self.mesh.area[None, :]).sum(axis=1)
 
     def run(self, W: np.ndarray, t_end: float, cfl: float):
-        """Step to t_end with N = ceil(t_end / dt_cfl) equal steps (dt from the initial state)."""
+        """Step from t = 0 to t_end with N = ceil(t_end / dt_cfl) equal steps (dt from the initial
+        state); the time after each step is the running sum of the steps."""
         dt0 = self.max_dt(W, cfl)
         n = int(np.ceil(t_end / dt0 - 1e-12))
         dt = t_end / n
+        t = 0.0
         for _ in range(n):
-            W = self.rk3_step(W, dt)
+            W = self.rk3_step(W, dt, t=t)
+            t += dt
         return W, n, dt

@@ -14,7 +14,7 @@ import math
 import numpy as np
 
 __all__ = ["scalar_wave", "density_wave", "isentropic_vortex", "four_quadrant_states", "riemann_exact",
-           "shock_tube", "shock_vortex",
+           "shock_tube", "shock_vortex", "moving_shock", "double_mach",
            "cell_average", "four_quadrant_average", "euler_prim_to_cons"]
 
 GAMMA = 1.4
@@ -176,6 +176,45 @@ def shock_vortex(x, y, t=0.0, mach=1.1, x_shock=0.5, center=(0.25, 0.5), kappa=0
     v = np.where(up, -kappa * eta * e * np.cos(th), 0.0)
     p = np.where(up, rho_up * T, p21)
     return euler_prim_to_cons(rho, u, v, p, gamma)
+
+
+def moving_shock(mach, x0, y0=0.0, angle_deg=90.0, pre=(1.4, 0.0, 0.0, 1.0), gamma=GAMMA):
+    """A straight shock through (x0, y0) at `angle_deg` to the x axis, moving at Mach `mach` into the
+    resting state `pre` (primitive rho, u, v, p), with the post-shock state of the normal-shock
+    (Rankine-Hugoniot) relations behind it.  The shock moves along its unit normal
+    n = (sin a, -cos a) at speed S = mach c_pre; behind it the gas moves along n at S (1 - rho1/rho2).
+
+    Returns dict(post, pre: primitive 4-tuples, line: (n_x, n_y, c0, S) such that the post-shock state
+    holds where n . x < c0 + S t, f: f(x, y, t) -> conservative state of this exact solution)."""
+    r1, u1, v1, p1 = (float(q) for q in pre)
+    assert u1 == 0.0 and v1 == 0.0, "the pre-shock gas is at rest"
+    a = math.radians(angle_deg)
+    nx, ny = math.sin(a), -math.cos(a)
+    m2 = mach * mach
+    c1 = math.sqrt(gamma * p1 / r1)
+    S = mach * c1
+    r2 = r1 * (gamma + 1) * m2 / ((gamma - 1) * m2 + 2)
+    p2 = p1 * (1 + 2 * gamma / (gamma + 1) * (m2 - 1))
+    w2 = S * (1 - r1 / r2)
+    post = (r2, w2 * nx, w2 * ny, p2)
+    c0 = nx * x0 + ny * y0
+
+    def f(x, y, t=0.0):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        behind = nx * x + ny * y < c0 + S * t
+        q = [np.where(behind, b, c) for b, c in zip(post, (r1, u1, v1, p1))]
+        return euler_prim_to_cons(*q, gamma)
+
+    return {"post": post, "pre": (r1, u1, v1, p1), "line": (nx, ny, c0, S), "f": f}
+
+
+def double_mach(gamma=GAMMA):
+    """The double Mach reflection set-up: a Mach 10 shock through (1/6, 0) at 60 degrees to the x axis
+    moving into (1.4, 0, 0, 1); post-shock (8, 4.125 sqrt 3, -4.125, 116.5).  Domain [0, 4] x [0, 1],
+    reflective wall on the bottom from x = 1/6, the exact post-shock state on the rest of the bottom
+    and on the left, the exact moving shock on the top, outflow on the right."""
+    return moving_shock(10.0, 1.0 / 6.0, 0.0, 60.0, gamma=gamma)
 
 
 def _gauss_legendre01(order: int):

@@ -34,6 +34,9 @@ class MeshInput:
     bc         "periodic" (both directions, period = extent) or "outflow"
     walls      outflow meshes: box sides that are reflective walls instead of outflow
                (0: x = origin_x, 1: x = origin_x + extent_x, 2: y = origin_y, 3: y = origin_y + extent_y)
+    wall_from  per side: the wall covers only the faces whose midpoint lies at least this far
+               along the side from the origin corner (y for sides 0, 1; x for sides 2, 3)
+    inflow     box sides whose faces that are not walls take a prescribed outer state
     """
     nodes: np.ndarray
     cell_ptr: np.ndarray
@@ -45,6 +48,8 @@ class MeshInput:
     seed: int = 0
     meta: dict = field(default_factory=dict)
     walls: tuple = ()
+    wall_from: tuple = (0.0, 0.0, 0.0, 0.0)
+    inflow: tuple = ()
 
     @property
     def n_cells(self) -> int:
@@ -208,14 +213,18 @@ def _vortex_maps(L: float, a: float = 9.0 / 11.0):
     return g, gy
 
 
-def tube_mesh(nx: int, ny: int, extent, kind="quad", delta=0.1, seed=0, walls=()):
+def tube_mesh(nx: int, ny: int, extent, kind="quad", delta=0.1, seed=0, walls=(), wall_from=(0.0, 0.0, 0.0, 0.0),
+              inflow=()):
     """Outflow box [0, Lx] x [0, Ly] of nx x ny perturbed quads (kind "quad"), all split into
-    triangles ("tri") or 30 % split ("mixed"); `walls` names reflective sides (see MeshInput)."""
+    triangles ("tri") or 30 % split ("mixed"); `walls`, `wall_from` and `inflow` name reflective and
+    inflow sides (see MeshInput)."""
     frac = {"quad": 0.0, "tri": 1.0, "mixed": 0.3}[kind]
     pos, quads = perturbed_quads(nx, (0.0, 0.0), tuple(extent), delta, seed, ny=ny)
     mi = _assemble(pos, quads, frac, seed, "outflow", (0.0, 0.0), tuple(extent), f"tube-{kind}-{nx}x{ny}",
                    {"nx": nx, "ny": ny, "split": frac, "delta": delta})
     mi.walls = tuple(walls)
+    mi.wall_from = tuple(float(v) for v in wall_from)
+    mi.inflow = tuple(inflow)
     return mi
 
 

@@ -71,8 +71,24 @@ def test_rk3_stability_polynomial():
     lam = -0.8 + 0.3j
     W = np.array([[1.0 + 0.5j, -2.0]])
     z = lam * 0.37
-    out = sol.rk3_step(W, 0.37, L=lambda w: lam * w)
+    out = sol.rk3_step(W, 0.37, L=lambda w, t: lam * w)
     assert np.allclose(out, W * (1 + z + z * z / 2 + z ** 3 / 6), rtol=1e-15)
+
+
+def test_rk3_stage_times_integrate_cubics_exactly():
+    """dW/dt = f(t): the three stages sit at t, t + dt, t + dt/2 with weights 1/6, 1/6, 2/3
+    (Simpson's rule), so one step integrates any cubic f exactly; a stage at the wrong time
+    (e.g. every stage at t) fails already for f(t) = t."""
+    mi = S.mesh_for_config(1, n=4)
+    sol = OracleSolver(OracleMesh.from_input(mi), Params(eqn="scalar"))
+    W = np.array([[0.25]])
+    for f, F in ((lambda t: 1.0 + 0.0 * t, lambda t: t), (lambda t: t, lambda t: t * t / 2),
+                 (lambda t: 3 * t * t - t, lambda t: t ** 3 - t * t / 2), (lambda t: 4 * t ** 3, lambda t: t ** 4)):
+        t0, dt = 0.7, 0.3
+        out = sol.rk3_step(W, dt, L=lambda w, t: np.full_like(w, f(t)), t=t0)
+        assert out[0, 0] == pytest.approx(0.25 + F(t0 + dt) - F(t0), rel=1e-14, abs=1e-14)
+    out = sol.rk3_step(W, 0.3, L=lambda w, t: np.full_like(w, t ** 4), t=0.7)   # quartic: Simpson's error
+    assert abs(out[0, 0] - (0.25 + (1.0 ** 5 - 0.7 ** 5) / 5)) > 1e-6
 
 
 @pytest.mark.parametrize("cfg,kind", [(2, "mixed"), (2, "tri"), (5, None)])

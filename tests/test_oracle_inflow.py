@@ -1,0 +1,111 @@
+"""Oracle pins of the prescribed-state (inflow) boundaries and partial walls of the double Mach
+reflection set-up (Section 4): the states the paper prints, the Rankine-Hugoniot relations of the
+moving shock, free-stream preservation, and a planar shock carried through the inflow sides by the
+time-dependent boundary state against the exact moving shock."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import OracleMesh, OracleSolver, Params
+from oracle.flux import euler_normal_flux, primitive_to_conservative
+
+GAMMA = 1.4
+
+
+def test_double_mach_states_match_the_paper():
+    """Section 4, double Mach reflection: post-shock (8, 4.125 sqrt 3, -4.125, 116.5), ambient
+    (1.4, 0, 0, 1); the shock meets the top side y = 1 at x = 1/6 + (1 + 20 t)/sqrt 3 (exact motion
+    of a Mach 10 shock at 60 degrees through (1/6, 0))."""
+    d = S.double_mach()
+    assert np.allclose(d["post"], (8.0, 4.125 * math.sqrt(3.0), -4.125, 116.5), rtol=1e-14)
+    assert d["pre"] == (1.4, 0.0, 0.0, 1.0)
+    nx, ny, c0, s = d["line"]
+    for t in (0.0, 0.05, 0.2):
+        xs = 1.0 / 6.0 + (1.0 + 20.0 * t) / math.sqrt(3.0)
+        assert nx * xs + ny * 1.0 == pytest.approx(c0 + s * t, abs=1e-13)
+        assert nx * (1.0 / 6.0) == pytest.approx(c0, abs=1e-15)  # through (1/6, 0) at t = 0
+
+
+@pytest.mark.parametrize("mach,angle", [(10.0, 60.0), (2.0, 90.0), (3.5, 30.0)])
+def test_moving_shock_satisfies_rankine_hugoniot(mach, angle):
+    """S [U] = [F(U) . n] across the moving shock (mass, momentum, energy)."""
+    d = S.moving_shock(mach, 0.3, 0.1, angle)
+    nx, ny, _, s = d["line"]
+    U2 = primitive_to_conservative(d["post"], GAMMA)
+    U1 = primitive_to_conservative(d["pre"], GAMMA)
+    F2 = euler_normal_flux(U2[:, None], np.array([nx]), np.array([ny]), GAMMA)[:, 0]
+    F1 = euler_normal_flux(U1[:, None], np.array([nx]), np.array([ny]), GAMMA)[:, 0]
+    assert np.allclose(s * (U2 - U1), F2 - F1, rtol=1e-13, atol=1e-12)
+    assert s == pytest.approx(mach, rel=1e-14)           # c = 1 in the ambient state
+
+
+def _box(kind="mixed", nx=24, ny=8, walls=(2,), wall_from=(0.0, 0.0, 0.25, 0.0), inflow=(0, 2, 3), delta=0.1):
+    return S.tube_mesh(nx, ny, (1.0, 1.0 / 3.0), kind, delta=delta, seed=3, walls=walls, wall_from=wall_from,
+                       inflow=inflow)
+
+
+def test_partial_wall_and_inflow_faces():
+    """A wall side with wall_from covers the faces whose midpoint lies at least that far along it;
+    the rest of an inflow side takes the prescribed state, the other sides stay outflow."""
+    mi = S.tube_mesh(40, 4, (1.0, 0.1), "quad", delta=0.1, seed=1, walls=(2,), wall_from=(0, 0, 0.25, 0),
+                     inflow=(0, 2, 3))
+    m = OracleMesh.from_input(mi)
+    bottom = m.face_side == 2
+    assert bottom.sum() == 40
+    assert (m.face_wall & bottom).sum() == 30                  # midpoints (i + 1/2)/40 >= 0.25
+    assert (m.face_inflow & bottom).sum() == 10
+    assert (m.face_inflow & (m.face_side == 0)).sum() == 4 and (m.face_inflow & (m.face_side == 3)).sum() == 40
+    assert not (m.face_inflow | m.face_wall)[m.face_side == 1].any()
+    assert not (m.face_inflow & m.face_wall).any()
+    with pytest.raises(ValueError):
+        OracleMesh(mi.nodes, mi.cell_ptr, mi.cell_nodes, "periodic", (0, 0), (1.0, 0.1), inflow=(0,))
+    with pytest.raises(ValueError):
+        OracleSolver(m, Params())                              # inflow faces need the states
+
+
+@pytest.mark.parametrize("kind", ["mixed", "tri"])
+def test_free_stream_through_inflow_sides_and_partial_wall(kind):
+    """A uniform supersonic stream parallel to the bottom wall, equal to the prescribed state:
+    L(W) = 0 to rounding on every cell (inflow faces: F(W) . n; walls: pressure only)."""
+    mi = _box(kind)
+    q = (1.3, 2.5, 0.0, 0.9)
+    sol = OracleSolver(OracleMesh.from_input(mi), Params(inflow_a=q, inflow_b=q, inflow_line=(0.6, 0.8, 0.3, 1.0)))
+    W = np.repeat(primitive_to_conservative(q, GAMMA)[:, None], mi.n_cells, axis=1)
+    R = sol.residual(W, t=0.37)
+    assert np.abs(R).max() < 1e-12 * np.abs(W).max() / (1.0 / 24)
+
+
+def _planar_shock_run(frozen=False, kind="quad"):
+    sh = S.moving_shock(2.0, 0.2)
+    mi = S.tube_mesh(40, 4, (1.0, 0.1), kind, delta=0.1, seed=1, inflow=(0, 2, 3))
+    m = OracleMesh.from_input(mi)
+    sol = OracleSolver(m, Params(inflow_a=sh["post"], inflow_b=sh["pre"], inflow_line=sh["line"]))
+    if frozen:                       # planted mistake: the boundary state never moves
+        sol.inflow_speed = 0.0
+    W, n, dt = sol.run(S.cell_average(mi, sh["f"]), 0.15, 0.5)
+    ex = S.cell_average(mi, lambda x, y: sh["f"](x, y, 0.15))
+    l1 = float(np.sum(np.abs(W[0] - ex[0]) * m.area) / m.area.sum())
+    # shock position: where the density crosses the mean of the two states, along the cell centroids
+    mid = 0.5 * (sh["post"][0] + sh["pre"][0])
+    c = m.centroid
+    xs = []
+    for row in range(4):
+        sel = np.flatnonzero(np.abs(c[:, 1] - (row + 0.5) * 0.025) < 0.0125)
+        sel = sel[np.argsort(c[sel, 0])]
+        r = W[0, sel]
+        k = int(np.flatnonzero((r[:-1] >= mid) & (r[1:] < mid))[-1])
+        xs.append(c[sel[k], 0] + (r[k] - mid) / (r[k] - r[k + 1]) * (c[sel[k + 1], 0] - c[sel[k], 0]))
+    return l1, np.array(xs), float(np.abs(W[2]).max())
+
+
+def test_planar_shock_carried_by_the_moving_boundary_state():
+    """A Mach 2 shock runs along a tube whose left, bottom and top sides take the exact moving-shock
+    state: at t = 0.15 it sits at x = 0.2 + 2 t = 0.5 on every row (to half a cell), the
+    density is within a smeared-shock L1 error of the exact solution, and the transverse momentum
+    stays small.  With the boundary state frozen at t = 0 (planted in the oracle) all three fail."""
+    l1, xs, rv = _planar_shock_run()
+    assert l1 < 0.09 and np.abs(xs - 0.5).max() < 0.025 / 2 and rv < 0.3, (l1, xs, rv)
+    l1, xs, rv = _planar_shock_run(frozen=True)
+    assert l1 > 0.3 and rv > 0.6, (l1, xs, rv)
