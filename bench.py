@@ -472,6 +472,88 @@ def run_shock_vortex(args):
     print(json.dumps({"shock_vortex": out, "t": T, "cfl": args.cfl}), flush=True)
 
 
+def _write_png(path, img):
+    """8-bit greyscale PNG of a 2D uint8 array (row 0 at the top)."""
+    import struct
+    import zlib
+    h, w = img.shape
+    raw = b"".join(b"\x00" + img[r].tobytes() for r in range(h))
+
+    def chunk(tag, data):
+        return struct.pack(">I", len(data)) + tag + data + struct.pack(">I", zlib.crc32(tag + data) & 0xFFFFFFFF)
+
+    with open(path, "wb") as f:
+        f.write(b"\x89PNG\r\n\x1a\n" + chunk(b"IHDR", struct.pack(">IIBBBBB", w, h, 8, 0, 0, 0, 0))
+                + chunk(b"IDAT", zlib.compress(raw, 6)) + chunk(b"IEND", b""))
+
+
+def run_dmr(args):
+    """The double Mach reflection of the paper's tests through the CUDA path: [0,4] x [0,1], Mach 10
+    shock at 60 degrees through (1/6, 0), reflective bottom wall from x = 1/6, exact post-shock state on
+    the left and on the bottom before x = 1/6, the exact moving shock on the top, outflow on the right;
+    t = 0.2, irregular quad and triangle meshes with h = 1/100, 1/200.  No exact solution: reports
+    completion, extrema, the incident shock's position on the top side against the exact
+    1/6 + (1 + 20 t)/sqrt 3, the foot of the Mach stem on the wall and (optionally) a density image."""
+    import torch
+    import synthetic as S
+    from paper_1712_08317_gb300.api import Mesh, Solver
+    T = 0.2
+    d = S.double_mach()
+    prm = dict(inflow_a=d["post"], inflow_b=d["pre"], inflow_line=d["line"])
+    mid = 0.5 * (d["post"][0] + d["pre"][0])
+    x_top = 1.0 / 6.0 + (1.0 + 20.0 * T) / np.sqrt(3.0)
+    out = []
+    for k in [int(x) for x in args.dmr_h.split(",")]:
+        for kind in ("quad", "tri"):
+            h = 1.0 / k
+            mi = S.tube_mesh(4 * k, k, (4.0, 1.0), kind, 0.1, seed=4, walls=(2,), wall_from=(0, 0, 1.0 / 6.0, 0),
+                             inflow=(0, 2, 3))
+            mesh = Mesh.from_input(mi)
+            W0 = S.cell_average(mi, d["f"], order=4)
+            cen = mi.nodes[mi.padded_cells()[0]].mean(axis=1)
+            top = cen[:, 1] > 1.0 - 0.75 * h
+            bot = cen[:, 1] < 0.75 * h
+            row = {"mesh": f"irregular {kind}", "h": f"1/{k}", "cells": mi.n_cells, "inflow_faces": mesh.info.n_inflow}
+            precs = [p for p in args.precisions.split(",") if p == "fp32c" or k <= args.dmr_fp64_max]
+            for ch in (False, True):
+                res = {}
+                for prec in precs:
+                    sol = Solver(mesh, eqn="euler", precision=prec, characteristic=ch, **prm)
+                    U, Ul = sol.to_device(W0)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    steps = _march(sol, U, Ul, T, args.cfl)
+                    torch.cuda.synchronize()
+                    secs = time.perf_counter() - t0
+                    try:
+                        sol.check()
+                    except Exception as exc:
+                        res[prec] = {"steps": steps, "failed": str(exc).split(":")[0]}
+                        continue
+                    W = sol.to_host(U, Ul)
+                    p = 0.4 * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
+                    r = {"steps": steps, "seconds": secs, "t": float(sol.get_time()[0]), "rho_min": float(W[0].min()),
+                         "rho_max": float(W[0].max()), "p_min": float(p.min()),
+                         "x_shock_top": float(cen[top & (W[0] > mid), 0].max()), "x_shock_top_exact": x_top,
+                         "x_mach_stem_wall": float(cen[bot & (W[0] > mid), 0].max()),
+                         "rho_max_wall": float(W[0][bot].max())}
+                    res[prec] = r
+                    if args.dmr_image_dir and prec == "fp32c":
+                        from scipy.spatial import cKDTree
+                        nx_px, ny_px = 3 * k, k            # [0, 3] x [0, 1], one pixel per h
+                        gx, gy = np.meshgrid((np.arange(nx_px) + 0.5) * h, 1.0 - (np.arange(ny_px) + 0.5) * h)
+                        _, idx = cKDTree(cen).query(np.stack([gx.ravel(), gy.ravel()], 1))
+                        rho = W[0][idx].reshape(ny_px, nx_px)
+                        img = np.clip((rho - 1.4) / (22.0 - 1.4) * 255.0, 0, 255).astype(np.uint8)
+                        os.makedirs(args.dmr_image_dir, exist_ok=True)
+                        _write_png(os.path.join(args.dmr_image_dir,
+                                                f"dmr_rho_{kind}_h{k}_{'char' if ch else 'comp'}.png"), img)
+                row["characteristic" if ch else "componentwise"] = res
+            out.append(row)
+            print(json.dumps({"dmr": row}), flush=True)
+    print(json.dumps({"dmr": out, "t": T, "cfl": args.cfl}), flush=True)
+
+
 def run_accuracy(args):
     """Convergence ladders to t = 2 through the CUDA path: FP64 and FP32C, L1 / Linf of rho vs exact."""
     ladders = {"densitywave-tri": [int(x) for x in args.ladder_dw.split(",")],
@@ -524,6 +606,10 @@ def parse_args(argv=None):
     ap.add_argument("--tubes", action="store_true", help="Sod and Lax shock tubes (walls top and bottom) vs exact")
     ap.add_argument("--ladder-tube", default="100,200")
     ap.add_argument("--shock-vortex", action="store_true", help="shock-vortex interaction (walls top and bottom)")
+    ap.add_argument("--dmr", action="store_true", help="double Mach reflection (inflow sides, partial wall)")
+    ap.add_argument("--dmr-h", default="100,200", help="1/h of the double Mach reflection meshes")
+    ap.add_argument("--dmr-fp64-max", type=int, default=100, help="largest 1/h run in FP64 as well")
+    ap.add_argument("--dmr-image-dir", default="", help="write density images (PNG) of the FP32C runs here")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     return ap.parse_args(argv)
 
@@ -541,6 +627,9 @@ def main():
         return
     if args.shock_vortex:
         run_shock_vortex(args)
+        return
+    if args.dmr:
+        run_dmr(args)
         return
     assert args.warmup >= 3, "at least 3 warm-up steps"
     import torch
@@ -749,7 +838,8 @@ def main():
         acc_t2 = {"family": "densitywave-tri", "t": 2.0, "cfl": 0.5,
                   **ladder_point("densitywave-tri", args.acc_n, ["fp64", "fp32c"])}
 
-    launches_per_step = 1 + 3 * ((1 if nQ else 0) + (1 if nT else 0) + 1 + (1 if nQ else 0) + (1 if nT else 0))
+    # k_fill of dt, the three stages, k_advance_time
+    launches_per_step = 2 + 3 * ((1 if nQ else 0) + (1 if nT else 0) + 1 + (1 if nQ else 0) + (1 if nT else 0))
     launch_cfg = sol.launch_config().tolist()
     del sol64, V
     batched = None

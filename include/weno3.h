@@ -75,6 +75,13 @@ typedef struct {
                         reversed, and the mirror images across it in the stencils (Sections
                         3.1, 3.2) carry the mirrored cell's average with that momentum
                         component reversed.  0 = every boundary face is outflow.            */
+  double wall_from[4]; /* per side s: the wall covers only the faces whose midpoint lies at
+                        least wall_from[s] along the side from the origin corner (y - origin[1]
+                        on sides 0, 1; x - origin[0] on sides 2, 3); 0 = the whole side.  The
+                        double Mach reflection's wall starts at x = 1/6 (Section 4).         */
+  int32_t inflow;    /* outflow meshes, Euler: bit s set = the faces of box side s that are not
+                        walls see a prescribed outer state in the flux (weno_params.inflow_*);
+                        the stencil images across them are the outflow ones.  0 = none.      */
 } weno_mesh_opts;
 
 /* Scheme parameters (defaults: weno_params_default). */
@@ -93,6 +100,17 @@ typedef struct {
   int32_t characteristic; /* Euler: 1 = reconstruct characteristic variables per face (Section 4:
                          normal flux Jacobian at the Roe average of the two cells), 0 =
                          component-wise (default)                                          */
+  /* Prescribed outer state of inflow faces (weno_mesh_opts.inflow), Euler only: primitive
+   * (rho, u, v, p) inflow_a at the Gauss points x of those faces with
+   * n_x x + n_y y < c0 + s t, inflow_b elsewhere, inflow_line = (n_x, n_y, c0, s), t the
+   * solver's time (weno_set_time, advanced by every step; the RK3 stages of Section 4 sit
+   * at t, t + dt, t + dt/2).  A constant state: inflow_a = inflow_b.  The double Mach
+   * reflection (Section 4) takes the post-shock state behind the moving Mach 10 shock and
+   * the ambient state ahead of it.  Both states need rho > 0 and p > 0 when the mesh has
+   * inflow faces; unused otherwise.  The comparison is made in FP64 in both precisions.   */
+  double inflow_a[4];
+  double inflow_b[4];
+  double inflow_line[4];
 } weno_params;
 
 typedef struct {
@@ -102,7 +120,7 @@ typedef struct {
   int64_t n_faces;      /* faces (periodic pairs counted once; outflow faces once)    */
   int64_t n_boundary;   /* outflow boundary faces                                     */
   int32_t n_instances;  /* 1, or the number of meshes joined by weno_mesh_concat      */
-  int32_t reserved;
+  int32_t n_inflow;     /* inflow faces (weno_mesh_opts.inflow)                       */
 } weno_mesh_info;
 
 /* Fills *p with the defaults: Euler, FP64, gamma 1.4, adv (1,1), eps 1e-6,
@@ -167,8 +185,8 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
 
 int weno_solver_get_info(weno_solver_t s, weno_mesh_info* info);
 
-/* R = L(U) (Eq. 4).  U, U_lo, R: device arrays [n_cells * n_v] (U_lo only
- * for FP32C, else NULL).  Stream-ordered. */
+/* R = L(U) (Eq. 4) at the solver's time.  U, U_lo, R: device arrays
+ * [n_cells * n_v] (U_lo only for FP32C, else NULL).  Stream-ordered. */
 int weno_residual(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream);
 
 /* R = L(U) exactly like weno_residual, but without touching any memory the
@@ -192,8 +210,18 @@ int weno_residual(weno_solver_t s, const void* U, const void* U_lo, void* R, voi
  * Stream-ordered. */
 int weno_residual_static(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream);
 
+/* Sets the solver's time (every instance) to t; it starts at 0.  The time
+ * enters only through inflow faces and advances by dt with every step.
+ * Stream-ordered. */
+int weno_set_time(weno_solver_t s, double t, void* cuda_stream);
+
+/* Copies the time of every instance to t_out [n_instances] (host);
+ * synchronises the stream. */
+int weno_get_time(weno_solver_t s, double* t_out, void* cuda_stream);
+
 /* One SSP-RK3 step (Section 4) of size dt in place on U (and U_lo). Uses a
  * CUDA graph of the three stages, built on first use for these pointers.
+ * The stages evaluate L at the times t, t + dt and t + dt/2; then t += dt.
  * Stream-ordered. */
 int weno_step(weno_solver_t s, void* U, void* U_lo, double dt, void* cuda_stream);
 

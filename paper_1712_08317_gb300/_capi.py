@@ -17,18 +17,20 @@ STATUS_NAMES = {0: "WENO_OK", -1: "WENO_EINVAL", -2: "WENO_EMESH", -3: "WENO_EPE
 
 
 class weno_mesh_opts(C.Structure):
-    _fields_ = [("bc", C.c_int32), ("origin", C.c_double * 2), ("extent", C.c_double * 2), ("walls", C.c_int32)]
+    _fields_ = [("bc", C.c_int32), ("origin", C.c_double * 2), ("extent", C.c_double * 2), ("walls", C.c_int32),
+                ("wall_from", C.c_double * 4), ("inflow", C.c_int32)]
 
 
 class weno_params(C.Structure):
     _fields_ = [("eqn", C.c_int32), ("precision", C.c_int32), ("gas_gamma", C.c_double), ("adv", C.c_double * 2),
                 ("eps", C.c_double), ("theta", C.c_double), ("rcond", C.c_double), ("optimize", C.c_int32),
-                ("linear", C.c_int32), ("n_threads", C.c_int32), ("characteristic", C.c_int32)]
+                ("linear", C.c_int32), ("n_threads", C.c_int32), ("characteristic", C.c_int32),
+                ("inflow_a", C.c_double * 4), ("inflow_b", C.c_double * 4), ("inflow_line", C.c_double * 4)]
 
 
 class weno_mesh_info(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_quads", C.c_int64), ("n_tris", C.c_int64), ("n_faces", C.c_int64),
-                ("n_boundary", C.c_int64), ("n_instances", C.c_int32), ("reserved", C.c_int32)]
+                ("n_boundary", C.c_int64), ("n_instances", C.c_int32), ("n_inflow", C.c_int32)]
 
 
 # exported symbols with (restype, argtypes)
@@ -47,6 +49,8 @@ SIGNATURES = {
     "weno_solver_get_info": (C.c_int, [P, C.POINTER(weno_mesh_info)]),
     "weno_residual": (C.c_int, [P, P, P, P, P]),
     "weno_residual_static": (C.c_int, [P, P, P, P, P]),
+    "weno_set_time": (C.c_int, [P, C.c_double, P]),
+    "weno_get_time": (C.c_int, [P, P, P]),
     "weno_step": (C.c_int, [P, P, P, C.c_double, P]),
     "weno_step_instances": (C.c_int, [P, P, P, P, P]),
     "weno_max_dt": (C.c_int, [P, P, P, C.c_double, P, P]),

@@ -23,7 +23,7 @@ class Mesh:
     """Host mesh (topology, renumbering, stencils) owned by the library."""
 
     def __init__(self, nodes, cell_ptr, cell_nodes, bc="periodic", origin=(0.0, 0.0), extent=(1.0, 1.0), walls=(),
-                 _handle=None):
+                 wall_from=(0.0, 0.0, 0.0, 0.0), inflow=(), _handle=None):
         self._lib = capi.load()
         if _handle is not None:
             self._h = _handle
@@ -36,6 +36,9 @@ class Mesh:
             opts.origin[0], opts.origin[1] = origin
             opts.extent[0], opts.extent[1] = extent
             opts.walls = sum(1 << int(w) for w in set(walls))
+            for k in range(4):
+                opts.wall_from[k] = float(wall_from[k])
+            opts.inflow = sum(1 << int(w) for w in set(inflow))
             h = C.c_void_p()
             capi.check(self._lib.weno_mesh_create(_ptr(nodes), nodes.shape[0], _ptr(cell_ptr), _ptr(cell_nodes),
                                                   cell_ptr.shape[0] - 1, C.byref(opts), C.byref(h)))
@@ -48,7 +51,8 @@ class Mesh:
 
     @classmethod
     def from_input(cls, mi):
-        return cls(mi.nodes, mi.cell_ptr, mi.cell_nodes, mi.bc, mi.origin, mi.extent, getattr(mi, "walls", ()))
+        return cls(mi.nodes, mi.cell_ptr, mi.cell_nodes, mi.bc, mi.origin, mi.extent, getattr(mi, "walls", ()),
+                   getattr(mi, "wall_from", (0.0, 0.0, 0.0, 0.0)), getattr(mi, "inflow", ()))
 
     @classmethod
     def concat(cls, meshes):
@@ -95,7 +99,8 @@ class Mesh:
 
 
 def params_struct(eqn="euler", precision="fp64", gas_gamma=1.4, adv=(1.0, 1.0), eps=1e-6, theta=3.0,
-                  rcond=1e-12, optimize=True, linear=False, n_threads=0, characteristic=False):
+                  rcond=1e-12, optimize=True, linear=False, n_threads=0, characteristic=False, inflow_a=None,
+                  inflow_b=None, inflow_line=(1.0, 0.0, 0.0, 0.0)):
     p = capi.weno_params()
     capi.load().weno_params_default(C.byref(p))
     p.eqn = capi.WENO_EQN_EULER if eqn == "euler" else capi.WENO_EQN_SCALAR
@@ -109,6 +114,10 @@ def params_struct(eqn="euler", precision="fp64", gas_gamma=1.4, adv=(1.0, 1.0), 
     p.linear = int(bool(linear))
     p.n_threads = n_threads
     p.characteristic = int(bool(characteristic))
+    for k in range(4):
+        p.inflow_a[k] = 0.0 if inflow_a is None else float(inflow_a[k])
+        p.inflow_b[k] = 0.0 if inflow_b is None else float(inflow_b[k])
+        p.inflow_line[k] = float(inflow_line[k])
     return p
 
 
@@ -180,6 +189,14 @@ class Solver:
             R = self._torch.empty_like(U)
         capi.check(self._lib.weno_residual(self._h, self._p(U), self._p(U_lo), self._p(R), self._stream(stream)))
         return R
+
+    def set_time(self, t: float, stream=None):
+        capi.check(self._lib.weno_set_time(self._h, float(t), self._stream(stream)))
+
+    def get_time(self, stream=None) -> np.ndarray:
+        out = np.empty(self.n_instances)
+        capi.check(self._lib.weno_get_time(self._h, _ptr(out), self._stream(stream)))
+        return out
 
     def step(self, U, U_lo, dt: float, stream=None):
         self._check_state(U, U_lo)

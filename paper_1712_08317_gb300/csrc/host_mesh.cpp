@@ -148,12 +148,15 @@ bool same_member(const Slot& a, const Slot& b) {
 }  // namespace
 
 int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const int64_t* cell_nodes,
-               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], int32_t walls, Mesh& out,
-               std::string& err) {
-  if (walls && (bc != WENO_BC_OUTFLOW || (walls & ~15) || !(extent[0] > 0.0 && extent[1] > 0.0))) {
-    err = "walls name sides (bits 0-3) of an outflow box with positive extent";
+               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], int32_t walls,
+               const double wall_from[4], int32_t inflow, Mesh& out, std::string& err) {
+  if ((walls || inflow) &&
+      (bc != WENO_BC_OUTFLOW || (walls & ~15) || (inflow & ~15) || !(extent[0] > 0.0 && extent[1] > 0.0))) {
+    err = "walls and inflow sides name sides (bits 0-3) of an outflow box with positive extent";
     return WENO_EINVAL;
   }
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(wall_from[k])) { err = "wall_from must be finite"; return WENO_EINVAL; }
   if (n_cells <= 0 || n_nodes <= 0) { err = "empty mesh"; return WENO_EINVAL; }
   if (n_cells > (int64_t)INT32_MAX / 8) { err = "too many cells for 32-bit indices"; return WENO_EINVAL; }
   if (bc == WENO_BC_PERIODIC && !(extent[0] > 0.0 && extent[1] > 0.0)) {
@@ -369,18 +372,24 @@ int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const
       m.fny.push_back(-dx / L);
       m.flen.push_back(L);
       m.cell_face[i * 4 + k] = f;
-      int8_t wall = -1;
-      if (x < 0 && walls) {
-        // a wall face lies, with both ends, on a side of the box named in `walls`
+      int8_t wall = -1, in = 0;
+      if (x < 0 && (walls | inflow)) {
+        // a face of a box side lies on it with both ends; on a side named in `walls` it is a wall
+        // when its midpoint lies at least wall_from[side] along the side, otherwise on a side
+        // named in `inflow` an inflow face
         const double tol = 1e-9 * std::max(extent[0], extent[1]);
         for (int side = 0; side < 4; ++side) {
-          const int axis = side / 2;
+          const int axis = side / 2, along = 1 - axis;
           const double line = origin[axis] + (side % 2 ? extent[axis] : 0.0);
-          if ((walls >> side & 1) && std::fabs(v[2 * k + axis] - line) <= tol && std::fabs(v[2 * k1 + axis] - line) <= tol)
-            wall = (int8_t)axis;
+          if (!(std::fabs(v[2 * k + axis] - line) <= tol && std::fabs(v[2 * k1 + axis] - line) <= tol)) continue;
+          const double t = 0.5 * (v[2 * k + along] + v[2 * k1 + along]) - origin[along];
+          const bool w = (walls >> side & 1) && t >= wall_from[side];
+          wall = w ? (int8_t)axis : (int8_t)-1;
+          in = !w && (inflow >> side & 1) ? 1 : 0;
         }
       }
       m.fwall.push_back(wall);
+      m.fin.push_back(in);
       if (x >= 0) m.cell_face[(int64_t)x * 4 + m.nb_face[i * 4 + k]] = f;
       else m.n_boundary++;
     }
@@ -480,6 +489,7 @@ int concat_meshes(const Mesh* const* meshes, int32_t n, Mesh& out, std::string& 
       m.fny.push_back(a.fny[f]);
       m.flen.push_back(a.flen[f]);
       m.fwall.push_back(a.fwall[f]);
+      m.fin.push_back(a.fin[f]);
     }
     for (int k = 0; k < a.n_inst; ++k) {
       m.inst_period.push_back(a.inst_period[2 * k]);

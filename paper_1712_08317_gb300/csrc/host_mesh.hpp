@@ -54,6 +54,7 @@ struct Mesh {
   std::vector<int8_t> fkL, fkR;
   std::vector<double> fnx, fny, flen;
   std::vector<int8_t> fwall;         // reflective wall faces: 0 on an x side, 1 on a y side; -1 otherwise
+  std::vector<int8_t> fin;           // 1: inflow face (prescribed outer state), 0 otherwise
 
   int64_t n() const { return nQ + nT; }
   bool is_quad(int64_t c) const { return c < nQ; }
@@ -62,8 +63,8 @@ struct Mesh {
 // Builds topology, renumbering, faces and stencils.  Returns a weno_status
 // code and fills err on failure.
 int build_mesh(const double* xy, int64_t n_nodes, const int64_t* cell_ptr, const int64_t* cell_nodes,
-               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], int32_t walls, Mesh& out,
-               std::string& err);
+               int64_t n_cells, int32_t bc, const double origin[2], const double extent[2], int32_t walls,
+               const double wall_from[4], int32_t inflow, Mesh& out, std::string& err);
 
 // Disjoint union (batched instances).
 int concat_meshes(const Mesh* const* meshes, int32_t n, Mesh& out, std::string& err);

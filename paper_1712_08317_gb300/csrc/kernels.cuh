@@ -10,11 +10,13 @@
 //     k_reconstruct_char_tma  FP32C Euler, characteristic variables (four lanes
 //                             per cell exchange variables by shuffles)
 //     k_reconstruct_char      FP64, characteristic variables
-//   k_face         one thread per face: two Gauss points, rotated HLLC
-//                  (Euler) or upwind (scalar) flux, |l|/2 (F1 + F2) (Eqs. 5-6);
-//                  at reflective walls the outer state is the inner one mirrored.
+//   k_face         one thread per face: two Gauss points, rotated HLLC (Euler) or
+//                  upwind (scalar) flux, |l|/2 (F1 + F2) (Eqs. 5-6); at reflective
+//                  walls the outer state is the inner one mirrored, at inflow faces
+//                  the prescribed state at the stage time.
 //   k_gather       one thread per cell: signed gather of its face fluxes
 //                  (Eq. 4, no atomics) fused with the RK3 stage (Section 4).
+//   k_advance_time after the third stage of a step: t += dt per instance.
 // The reconstruction kernels take WALLS = true on meshes with reflective walls:
 // stencil entries then carry momentum flips for mirror images.
 //
@@ -615,18 +617,43 @@ __device__ __forceinline__ void hllc(const T wl[4], const T wr[4], T nx, T ny, T
 }
 
 
+// Prescribed outer state of the inflow faces (gr = -3 - q for inflow face q): wa at
+// the Gauss points whose xi = n . x_G - c0 (FP64, [q][2]) lies below speed * t_stage,
+// wb elsewhere; t_stage = t[instance] + c dt[instance] with c = 0, 1, 1/2 for the
+// three RK3 stages (Section 4).  The comparison is made in FP64 in both precisions.
+template <typename T>
+struct Inflow {
+  T wa[4], wb[4];
+  const double* xi;
+  const double* t;
+  const double* dt;
+  double speed, c;
+};
+
+__device__ __forceinline__ int64_t cell_of_gauss(int64_t g, int64_t nQ) {
+  return g < 8 * nQ ? g / 8 : nQ + (g - 8 * nQ) / 6;
+}
+
 // flag[instance] is set when a Gauss-point state of a face of that instance is
 // non-physical; nQ and inst map the left Gauss-value index back to its cell's
-// instance (inst == nullptr: a single instance).
-template <typename T, int NV>
+// instance (inst == nullptr: a single instance).  INFLOW: the mesh has inflow faces.
+template <typename T, int NV, bool INFLOW>
 __global__ void __launch_bounds__(256) k_face(
     const T* __restrict__ Wg, const int32_t* __restrict__ gl, const int32_t* __restrict__ gr,
     const T* __restrict__ fnx, const T* __restrict__ fny, const T* __restrict__ flen, int64_t nF,
-    T* __restrict__ F, Prm<T> prm, int* __restrict__ flag, const int32_t* __restrict__ inst, int64_t nQ) {
+    T* __restrict__ F, Prm<T> prm, int* __restrict__ flag, const int32_t* __restrict__ inst, int64_t nQ,
+    Inflow<T> inf) {
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nF; f += (int64_t)gridDim.x * blockDim.x) {
     bool bad = false;
     const int64_t il = __ldg(gl + f);
     const int64_t ir = __ldg(gr + f);
+    double t_stage = 0.0;
+    if constexpr (INFLOW) {
+      if (ir <= -3) {
+        const int i = inst ? __ldg(inst + cell_of_gauss(il, nQ)) : 0;
+        t_stage = inf.t[i] + inf.c * inf.dt[i];
+      }
+    }
     const T nx = __ldg(fnx + f), ny = __ldg(fny + f), len = __ldg(flen + f);
     T acc[NV];
 #pragma unroll
@@ -645,6 +672,13 @@ __global__ void __launch_bounds__(256) k_face(
           wr[1] = wl[1] - T(2) * mn * nx;
           wr[2] = wl[2] - T(2) * mn * ny;
         }
+        if constexpr (INFLOW && NV == 4) {
+          if (ir <= -3) {
+            const bool a = __ldg(inf.xi + 2 * (-3 - ir) + k) < inf.speed * t_stage;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) wr[v] = a ? inf.wa[v] : inf.wb[v];
+          }
+        }
       }
       if (NV == 4) {
         hllc<T>(wl, wr, nx, ny, prm.gas_gamma, fk, bad);
@@ -659,11 +693,14 @@ __global__ void __launch_bounds__(256) k_face(
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] *= T(0.5) * len;
     store_vec<T, NV>(F + f * NV, acc);
-    if (bad) {  // every writer stores the same value
-      const int64_t cl = il < 8 * nQ ? il / 8 : nQ + (il - 8 * nQ) / 6;
-      flag[inst ? __ldg(inst + cl) : 0] = 1;
-    }
+    if (bad) flag[inst ? __ldg(inst + cell_of_gauss(il, nQ)) : 0] = 1;  // every writer stores the same value
   }
+}
+
+// t[i] += dt[i] for every instance (after the third stage of a step).
+__global__ void k_advance_time(double* __restrict__ t, const double* __restrict__ dt, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) t[i] += dt[i];
 }
 
 // ---------------------------------------------------------------- K1, characteristic variables

@@ -104,6 +104,10 @@ struct weno_solver_s {
   // scratch
   void *Wg = nullptr, *F = nullptr, *Ws = nullptr, *Wslo = nullptr;
   double *dt_dev = nullptr, *red = nullptr, *cell_dt = nullptr;
+  double* t_dev = nullptr;   // time of each instance (advanced by every step)
+  int64_t n_in = 0;          // inflow faces
+  double* in_xi = nullptr;   // [n_in][2] n . x_G - c0 of their Gauss points
+  double in_wa[4] = {}, in_wb[4] = {};  // prescribed conservative states
   int* flag = nullptr;
   int debug_stall = 0;  // weno_solver_debug_stall
   bool walls = false;   // the mesh has reflective wall faces (stencil values carry momentum flips)
@@ -233,13 +237,34 @@ void launch_reconstruct(S& s, const void* U, const void* Ulo, cudaStream_t st, i
   launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, s.Wg, st, which);
 }
 
-template <typename T, int NV, bool COMP>
-void launch_face(S& s, cudaStream_t st) {
+// Face fluxes of the Gauss values wg into fl; c places the stage in the step (time t + c dt).
+template <typename T, int NV>
+void launch_face_into(S& s, const void* wg, void* fl, double c, cudaStream_t st) {
+  if (!s.nF) return;
   weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
-  if (s.nF)
-    weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
-        (const T*)s.Wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)s.F, p, s.flag,
-        s.inst, s.nQ);
+  weno::dev::Inflow<T> in{};
+  for (int v = 0; v < 4; ++v) {
+    in.wa[v] = (T)s.in_wa[v];
+    in.wb[v] = (T)s.in_wb[v];
+  }
+  in.xi = s.in_xi;
+  in.t = s.t_dev;
+  in.dt = s.dt_dev;
+  in.speed = s.prm.inflow_line[3];
+  in.c = c;
+  if (s.n_in)
+    weno::dev::k_face<T, NV, true><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
+        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
+        s.inst, s.nQ, in);
+  else
+    weno::dev::k_face<T, NV, false><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
+        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
+        s.inst, s.nQ, in);
+}
+
+template <typename T, int NV, bool COMP>
+void launch_face(S& s, cudaStream_t st, double c = 0.0) {
+  launch_face_into<T, NV>(s, s.Wg, s.F, c, st);
 }
 
 template <typename T, int NV, bool COMP, int MODE>
@@ -268,13 +293,16 @@ void launch_gather(S& s, int mode, void* U, void* Ulo, void* R, cudaStream_t st,
 
 template <typename T, int NV, bool COMP>
 void launch_step_body(S& s, void* U, void* Ulo, cudaStream_t st) {
+  // the stages of Section 4 evaluate L at t, t + dt, t + dt/2
+  constexpr double kStageTime[3] = {0.0, 1.0, 0.5};
   for (int stage = 1; stage <= 3; ++stage) {
     const void* src = stage == 1 ? U : s.Ws;
     const void* srclo = stage == 1 ? Ulo : s.Wslo;
     launch_reconstruct<T, NV, COMP>(s, src, srclo, st);
-    launch_face<T, NV, COMP>(s, st);
+    launch_face<T, NV, COMP>(s, st, kStageTime[stage - 1]);
     launch_gather<T, NV, COMP>(s, stage, U, Ulo, nullptr, st);
   }
+  weno::dev::k_advance_time<<<(s.n_inst + 127) / 128, 128, 0, st>>>(s.t_dev, s.dt_dev, s.n_inst);
 }
 
 // one call per precision / variable count
@@ -496,7 +524,7 @@ int weno_mesh_create(const double* node_xy, int64_t n_nodes, const int64_t* cell
     auto m = std::make_unique<weno_mesh_s>();
     std::string err;
     int r = weno::build_mesh(node_xy, n_nodes, cell_ptr, cell_nodes, n_cells, opts->bc, opts->origin, opts->extent,
-                             opts->walls, m->m, err);
+                             opts->walls, opts->wall_from, opts->inflow, m->m, err);
     if (r) return fail(r, err);
     *out = m.release();
   } catch (const std::bad_alloc&) {
@@ -534,7 +562,7 @@ int weno_mesh_get_info(weno_mesh_t mesh, weno_mesh_info* info) {
   info->n_faces = m.nF;
   info->n_boundary = m.n_boundary;
   info->n_instances = m.n_inst;
-  info->reserved = 0;
+  info->n_inflow = (int32_t)std::count(m.fin.begin(), m.fin.end(), (int8_t)1);
   return WENO_OK;
 }
 
@@ -631,6 +659,12 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
     return fail(WENO_EINVAL, "characteristic variables are defined for the Euler equations only");
   const bool walls = std::any_of(mesh->m.fwall.begin(), mesh->m.fwall.end(), [](int8_t w) { return w >= 0; });
   if (walls && p.eqn != WENO_EQN_EULER) return fail(WENO_EINVAL, "reflective walls are defined for the Euler equations only");
+  const int64_t n_in = std::count(mesh->m.fin.begin(), mesh->m.fin.end(), (int8_t)1);
+  if (n_in && p.eqn != WENO_EQN_EULER) return fail(WENO_EINVAL, "inflow faces are defined for the Euler equations only");
+  if (n_in && !(p.inflow_a[0] > 0 && p.inflow_a[3] > 0 && p.inflow_b[0] > 0 && p.inflow_b[3] > 0 &&
+                std::isfinite(p.inflow_a[1] + p.inflow_a[2] + p.inflow_b[1] + p.inflow_b[2]) &&
+                std::isfinite(p.inflow_line[0] + p.inflow_line[1] + p.inflow_line[2] + p.inflow_line[3])))
+    return fail(WENO_EINVAL, "inflow faces need both prescribed states with rho > 0, p > 0 and a finite line");
   const Mesh& m = mesh->m;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::unique_ptr<S> s;
@@ -643,6 +677,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   CK(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
   s->prm = p;
   s->walls = walls;
+  s->n_in = n_in;
   if (!(s->prm.rcond > 0)) s->prm.rcond = 1e-12;
   s->nv = p.eqn == WENO_EQN_EULER ? 4 : 1;
   s->fp64 = p.precision == WENO_FP64;
@@ -725,6 +760,34 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
       gl[f] = (int32_t)(gbase(m.fL[f]) + 2 * m.fkL[f]);
       gr[f] = m.fR[f] >= 0 ? (int32_t)(gbase(m.fR[f]) + 2 * m.fkR[f]) : (m.fwall[f] >= 0 ? -2 : -1);
     }
+    // inflow faces: gr = -3 - q, and n . x_G - c0 of their two Gauss points (edge k of the
+    // L cell: point 0 near node k, point 1 near node k + 1, Eq. 5)
+    std::vector<double> xi;
+    const double ga = (3.0 + std::sqrt(3.0)) / 6.0, gb = (3.0 - std::sqrt(3.0)) / 6.0;
+    const double* ln = p.inflow_line;
+    for (int64_t f = 0; f < d.nF; ++f) {
+      if (!m.fin[f]) continue;
+      gr[f] = (int32_t)(-3 - (int64_t)xi.size() / 2);
+      const int64_t c = m.fL[f];
+      const int k = m.fkL[f], k1 = (k + 1) % m.nvert[c];
+      const double* v = &m.verts[(size_t)c * 8];
+      for (int q = 0; q < 2; ++q) {
+        const double wa = q == 0 ? ga : gb, wb = q == 0 ? gb : ga;
+        const double x = wa * v[2 * k] + wb * v[2 * k1], y = wa * v[2 * k + 1] + wb * v[2 * k1 + 1];
+        xi.push_back(ln[0] * x + ln[1] * y - ln[2]);
+      }
+    }
+    if (d.n_in) {
+      if ((r = upload(d, &d.in_xi, xi, st))) return r;
+      auto cons = [&](const double* q, double* w) {
+        w[0] = q[0];
+        w[1] = q[0] * q[1];
+        w[2] = q[0] * q[2];
+        w[3] = q[3] / (p.gas_gamma - 1.0) + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2]);
+      };
+      cons(p.inflow_a, d.in_wa);
+      cons(p.inflow_b, d.in_wb);
+    }
     if ((r = upload(d, &d.gl, gl, st))) return r;
     if ((r = upload(d, &d.gr, gr, st))) return r;
     if ((r = upload_real(d, &d.fnx, m.fnx, st))) return r;
@@ -770,6 +833,9 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   if ((r = d.alloc(&d.Ws, (size_t)d.N * d.nv * d.esz))) return r;
   if (!d.fp64 && (r = d.alloc(&d.Wslo, (size_t)d.N * d.nv * d.esz))) return r;
   if ((r = d.alloc(&d.dt_dev, sizeof(double) * d.n_inst))) return r;
+  if ((r = d.alloc(&d.t_dev, sizeof(double) * d.n_inst))) return r;
+  CK(cudaMemsetAsync(d.t_dev, 0, sizeof(double) * d.n_inst, st));
+  CK(cudaMemsetAsync(d.dt_dev, 0, sizeof(double) * d.n_inst, st));
   if ((r = d.alloc(&d.red, sizeof(double) * d.n_inst * d.nv))) return r;
   if ((r = d.alloc(&d.cell_dt, sizeof(double) * d.N))) return r;
   if ((r = d.alloc(&d.flag, sizeof(int) * d.n_inst))) return r;
@@ -791,7 +857,7 @@ int weno_solver_get_info(weno_solver_t s, weno_mesh_info* info) {
   info->n_faces = s->nF;
   info->n_boundary = s->n_boundary;
   info->n_instances = s->n_inst;
-  info->reserved = 0;
+  info->n_inflow = (int32_t)s->n_in;
   return WENO_OK;
 }
 
@@ -831,6 +897,23 @@ int weno_step_instances(weno_solver_t s, void* U, void* U_lo, const double* dt_d
     exec = s->graphs.back().exec;
   }
   CK(cudaGraphLaunch(exec, st));
+  return WENO_OK;
+}
+
+int weno_set_time(weno_solver_t s, double t, void* cuda_stream) {
+  if (!s || !std::isfinite(t)) return fail(WENO_EINVAL, "null solver or non-finite time");
+  DeviceGuard g(s->dev);
+  weno::dev::k_fill<<<(s->n_inst + 127) / 128, 128, 0, (cudaStream_t)cuda_stream>>>(s->t_dev, t, s->n_inst);
+  CK(cudaGetLastError());
+  return WENO_OK;
+}
+
+int weno_get_time(weno_solver_t s, double* t_out, void* cuda_stream) {
+  if (!s || !t_out) return fail(WENO_EINVAL, "null argument");
+  DeviceGuard g(s->dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(cudaMemcpyAsync(t_out, s->t_dev, sizeof(double) * s->n_inst, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return WENO_OK;
 }
 
@@ -1048,11 +1131,7 @@ int static_scratch_base(int dev, void** base) {
 template <typename T, int NV, bool COMP>
 void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void* wg, void* fl, cudaStream_t st) {
   launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, wg, st, 3);
-  weno::dev::Prm<T> p{(T)s.prm.gas_gamma, (T)s.prm.adv[0], (T)s.prm.adv[1]};
-  if (s.nF)
-    weno::dev::k_face<T, NV><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
-        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
-        s.inst, s.nQ);
+  launch_face_into<T, NV>(s, wg, fl, 0.0, st);
   if (s.nQ)
     weno::dev::k_gather<T, NV, 4, COMP, 0><<<grid_of(s.k3q, s.nQ), s.k3q.block, 0, st>>>(
         (const T*)fl, s.q_cf, (const T*)s.inv_area, (const T*)s.inv_area_lo, s.nQ, 0, nullptr, nullptr, nullptr,

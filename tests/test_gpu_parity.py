@@ -390,3 +390,91 @@ def test_raw_linear_weights_match_oracle(name):
     U, Ul = s32.to_device(W)
     assert _rel(s32.to_host(s32.residual(U, Ul)), ref) < 2e-3
 
+
+
+# ---------------------------------------------------------------- inflow sides, partial wall, moving state
+def _inflow_case(kind="mixed", n=12):
+    """A small double-Mach-like box: a Mach 2.5 shock at 60 degrees through (0.3, 0) running into
+    gas at rest; bottom wall from x = 0.5, prescribed moving-shock state on the left, the rest of the
+    bottom and the top, outflow on the right.  Within 10 steps the shock crosses top-side Gauss
+    points, so the stage times decide some boundary states."""
+    sh = S.moving_shock(2.5, 0.3, 0.0, 60.0)
+    mi = S.tube_mesh(3 * n, n, (3.0, 1.0), kind, delta=0.1, seed=9, walls=(2,), wall_from=(0, 0, 0.5, 0),
+                     inflow=(0, 2, 3))
+    W = S.cell_average(mi, sh["f"])
+    prm = dict(inflow_a=sh["post"], inflow_b=sh["pre"], inflow_line=sh["line"])
+    return mi, W, prm
+
+
+@pytest.mark.parametrize("characteristic", [False, True])
+@pytest.mark.parametrize("kind", ["mixed", "quad"])
+def test_inflow_fp64_residual_and_steps_match_oracle(kind, characteristic):
+    mi, W, prm = _inflow_case(kind)
+    osol = OracleSolver(OracleMesh.from_input(mi), Params(characteristic=characteristic, **prm))
+    t0 = 0.013
+    dt = osol.max_dt(W, 0.5)
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp64", characteristic=characteristic, **prm)
+    assert sol.mesh.info.n_inflow == int(osol.mesh.face_inflow.sum())
+    sol.set_time(t0)
+    U, _ = sol.to_device(W)
+    assert _rel(sol.to_host(sol.residual(U)), osol.residual(W, t=t0)) < TOL_FP64
+    ref, t = W, t0
+    for _ in range(10):
+        ref = osol.rk3_step(ref, dt, t=t)
+        t += dt
+    for _ in range(10):
+        sol.step(U, None, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    assert _rel_cell(sol.to_host(U), ref) < TOL_FP64
+    assert sol.get_time()[0] == t
+    # the boundary state did move: the same steps with the time frozen at t0 differ
+    frozen = W
+    for _ in range(10):
+        frozen = osol.rk3_step(frozen, dt, t=t0)
+    assert _rel_cell(frozen, ref) > 1e-3
+
+
+@pytest.mark.parametrize("characteristic", [False, True])
+def test_inflow_fp32c_tracks_the_oracle(characteristic):
+    mi, W, prm = _inflow_case("mixed")
+    osol = OracleSolver(OracleMesh.from_input(mi), Params(characteristic=characteristic, **prm))
+    dt = osol.max_dt(W, 0.5)
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c", characteristic=characteristic, **prm)
+    U, Ul = sol.to_device(W)
+    assert _rel(sol.to_host(sol.residual(U, Ul)), osol.residual(W)) < 2e-3
+    ref, t = W, 0.0
+    for _ in range(10):
+        ref = osol.rk3_step(ref, dt, t=t)
+        t += dt
+    for _ in range(10):
+        sol.step(U, Ul, dt)
+    torch.cuda.synchronize()
+    sol.check()
+    assert _rel_cell(sol.to_host(U, Ul), ref) < 2e-6
+
+
+def test_batched_instances_with_inflow_keep_their_own_time():
+    """An inflow instance batched with a periodic one, different dt per instance, equals standalone
+    runs bit for bit (FP32C), and each instance's time advances by its own dt."""
+    a, wa, prm = _inflow_case("mixed", n=8)
+    b = S.mesh_for_config(2, n=9, seed=5, kind="tri")
+    wb = S.cell_average(b, S.density_wave)
+    meshes = [Mesh.from_input(a), Mesh.from_input(b)]
+    singles = [Solver(m, eqn="euler", precision="fp32c", **prm) for m in meshes]
+    states = [s.to_device(w) for s, w in zip(singles, (wa, wb))]
+    dts = [s.max_dt(U, Ul, 0.4)[0] for s, (U, Ul) in zip(singles, states)]
+    for s, (U, Ul), dt in zip(singles, states, dts):
+        for _ in range(4):
+            s.step(U, Ul, dt)
+    big = Solver(Mesh.concat(meshes), eqn="euler", precision="fp32c", **prm)
+    U, Ul = big.to_device(np.concatenate([wa, wb], axis=1))
+    dt_dev = torch.tensor(dts, dtype=torch.float64, device="cuda")
+    for _ in range(4):
+        big.step_instances(U, Ul, dt_dev)
+    torch.cuda.synchronize()
+    out = big.to_host(U, Ul)
+    assert np.array_equal(out[:, :a.n_cells], singles[0].to_host(*states[0]))
+    assert np.array_equal(out[:, a.n_cells:], singles[1].to_host(*states[1]))
+    t = big.get_time()
+    assert t[0] == dts[0] + dts[0] + dts[0] + dts[0] and t[1] == dts[1] + dts[1] + dts[1] + dts[1]

@@ -141,3 +141,27 @@ def test_wall_options_are_validated(lib):
         with pytest.raises(_capi.WenoError) as e:
             Mesh(mi.nodes, mi.cell_ptr, mi.cell_nodes, bc, (0.0, 0.0), extent, walls=walls)
         assert e.value.code == _capi.WENO_EINVAL
+
+
+@pytest.mark.parametrize("kind", ["quad", "mixed", "tri"])
+def test_inflow_faces_and_partial_walls_match_the_oracle(kind):
+    """Inflow sides and walls starting part-way along a side classify the same faces as the oracle."""
+    from paper_1712_08317_gb300.api import Mesh
+    for walls, wall_from, inflow in (((2,), (0, 0, 0.25, 0), (0, 2, 3)), ((), (0, 0, 0, 0), (1,)),
+                                     ((0, 2), (0.1, 0, 0.5, 0), (0, 1, 2, 3))):
+        mi = S.tube_mesh(20, 6, (1.0, 0.3), kind, delta=0.1, seed=4, walls=walls, wall_from=wall_from, inflow=inflow)
+        om = OracleMesh.from_input(mi)
+        m = Mesh.from_input(mi)
+        assert m.info.n_inflow == int(om.face_inflow.sum()) > 0
+        assert m.info.n_boundary == int((om.face_R < 0).sum())
+
+
+def test_inflow_options_are_validated(lib):
+    from paper_1712_08317_gb300 import _capi
+    from paper_1712_08317_gb300.api import Mesh
+    mi = S.mesh_for_config(3, n=6, seed=1, kind="mixed")
+    for bc, inflow, wall_from in (("periodic", (1,), (0, 0, 0, 0)), ("outflow", (5,), (0, 0, 0, 0)),
+                                  ("outflow", (1,), (0, float("nan"), 0, 0))):
+        with pytest.raises(_capi.WenoError) as e:
+            Mesh(mi.nodes, mi.cell_ptr, mi.cell_nodes, bc, (0.0, 0.0), (1.0, 1.0), inflow=inflow, wall_from=wall_from)
+        assert e.value.code == _capi.WENO_EINVAL
