@@ -252,14 +252,17 @@ void launch_face_into(S& s, const void* wg, void* fl, double c, cudaStream_t st)
   in.dt = s.dt_dev;
   in.speed = s.prm.inflow_line[3];
   in.c = c;
-  if (s.n_in)
-    weno::dev::k_face<T, NV, true><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
-        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
-        s.inst, s.nQ, in);
-  else
-    weno::dev::k_face<T, NV, false><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
-        (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
-        s.inst, s.nQ, in);
+  if constexpr (NV == 4) {  // inflow faces exist for the Euler equations only
+    if (s.n_in) {
+      weno::dev::k_face<T, NV, true><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
+          (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
+          s.inst, s.nQ, in);
+      return;
+    }
+  }
+  weno::dev::k_face<T, NV, false><<<grid_of(s.k2, s.nF), s.k2.block, 0, st>>>(
+      (const T*)wg, s.gl, s.gr, (const T*)s.fnx, (const T*)s.fny, (const T*)s.flen, s.nF, (T*)fl, p, s.flag,
+      s.inst, s.nQ, in);
 }
 
 template <typename T, int NV, bool COMP>
