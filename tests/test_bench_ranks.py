@@ -63,3 +63,25 @@ def test_reference_arm_runs_on_rank_zero_only():
     p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""                            # rank 1: no work, no line
+
+
+def test_density_image_is_a_valid_png(tmp_path):
+    """bench.py --dmr writes greyscale PNGs with its own encoder: signature, IHDR and a zlib stream
+    that inflates back to the filtered rows."""
+    import struct
+    import zlib
+    import numpy as np
+    import bench
+    img = (np.arange(6 * 5) * 7 % 256).astype(np.uint8).reshape(5, 6)
+    path = tmp_path / "x.png"
+    bench._write_png(str(path), img)
+    b = path.read_bytes()
+    assert b[:8] == b"\x89PNG\r\n\x1a\n"
+    n, tag = struct.unpack(">I4s", b[8:16])
+    assert tag == b"IHDR" and struct.unpack(">IIBBBBB", b[16:16 + n]) == (6, 5, 8, 0, 0, 0, 0)
+    i = b.index(b"IDAT")
+    m = struct.unpack(">I", b[i - 4:i])[0]
+    raw = zlib.decompress(b[i + 4:i + 4 + m])
+    rows = np.frombuffer(raw, np.uint8).reshape(5, 7)
+    assert (rows[:, 0] == 0).all() and np.array_equal(rows[:, 1:], img)
+    assert zlib.crc32(b[i:i + 4 + m]) & 0xFFFFFFFF == struct.unpack(">I", b[i + 4 + m:i + 8 + m])[0]
