@@ -109,3 +109,26 @@ def test_planar_shock_carried_by_the_moving_boundary_state():
     assert l1 < 0.09 and np.abs(xs - 0.5).max() < 0.025 / 2 and rv < 0.3, (l1, xs, rv)
     l1, xs, rv = _planar_shock_run(frozen=True)
     assert l1 > 0.3 and rv > 0.6, (l1, xs, rv)
+
+
+def test_double_mach_initial_shock_positivity_finding():
+    """Recorded behaviour of the scheme (no limiter) on the double Mach data at t = 0: Gauss values
+    with p <= 0 appear on cells straddling the Mach 10 shock for triangles with either variable set and
+    for quads component-wise, but not for quads with characteristic variables, the only combination
+    that runs to t = 0.2 through the CUDA path."""
+    d = S.double_mach()
+    bad = {}
+    for kind in ("tri", "quad"):
+        mi = S.tube_mesh(40, 20, (1.0, 0.5), kind, 0.1, seed=4, walls=(2,), wall_from=(0, 0, 1.0 / 6.0, 0),
+                         inflow=(0, 2, 3))
+        m = OracleMesh.from_input(mi)
+        W = S.cell_average(mi, d["f"], order=4)
+        for ch in (False, True):
+            sol = OracleSolver(m, Params(characteristic=ch, inflow_a=d["post"], inflow_b=d["pre"],
+                                         inflow_line=d["line"]))
+            Wg = sol.gauss_values(W)
+            p = (GAMMA - 1.0) * (Wg[3] - 0.5 * (Wg[1] ** 2 + Wg[2] ** 2) / Wg[0])
+            lo = np.where(np.isfinite(p), np.minimum(p, Wg[0]), np.inf).min(axis=1)
+            bad[kind, ch] = int((lo <= 0).sum())
+    assert bad["tri", False] > 0 and bad["tri", True] > 0 and bad["quad", False] > 0, bad
+    assert bad["quad", True] == 0, bad
