@@ -421,7 +421,7 @@ def run_tubes(args):
 def run_shock_vortex(args):
     """The shock-vortex interaction of the paper's tests through the CUDA path: [0,2] x [0,1],
     stationary Mach 1.1 shock at x = 0.5, vortex at (0.25, 0.5), reflective top and bottom
-    walls, outflow (zero-gradient) left and right, t = 0.8, h = 1/100 on irregular quad and
+    walls, outflow (zero-gradient) left and right, t = 0.8, h = 1/sv_h on irregular quad and
     triangle meshes.  No exact solution: reports completion, extrema, the FP32C-FP64 L1
     difference and the density on the centre line."""
     import torch
@@ -430,7 +430,7 @@ def run_shock_vortex(args):
     T = 0.8
     out = []
     for kind in ("quad", "tri"):
-        mi = S.tube_mesh(200, 100, (2.0, 1.0), kind, 0.1, seed=4, walls=(2, 3))
+        mi = S.tube_mesh(2 * args.sv_h, args.sv_h, (2.0, 1.0), kind, 0.1, seed=4, walls=(2, 3))
         mesh = Mesh.from_input(mi)
         W0 = S.cell_average(mi, S.shock_vortex, order=4)
         area = _cell_areas(mi)
@@ -606,6 +606,7 @@ def parse_args(argv=None):
     ap.add_argument("--tubes", action="store_true", help="Sod and Lax shock tubes (walls top and bottom) vs exact")
     ap.add_argument("--ladder-tube", default="100,200")
     ap.add_argument("--shock-vortex", action="store_true", help="shock-vortex interaction (walls top and bottom)")
+    ap.add_argument("--sv-h", type=int, default=100, help="1/h of the shock-vortex meshes (the paper shows 200)")
     ap.add_argument("--dmr", action="store_true", help="double Mach reflection (inflow sides, partial wall)")
     ap.add_argument("--dmr-h", default="100,200", help="1/h of the double Mach reflection meshes")
     ap.add_argument("--dmr-fp64-max", type=int, default=100, help="largest 1/h run in FP64 as well")
