@@ -31,3 +31,14 @@ def test_shu_osher_initial_data():
     assert np.allclose([rho[1], u[1], p[1]], [r, ul, pl], rtol=1e-14)     # x <= 1 is the left state
     assert np.allclose(rho[2:], 1.0 + 0.2 * np.sin(5.0 * x[2:]), rtol=1e-14)
     assert np.allclose(u[2:], 0.0) and np.allclose(p[2:], 1.0, rtol=1e-14)
+
+
+def test_shock_vortex_parameters():
+    import inspect
+
+    import synthetic as S
+    sig = inspect.signature(S.shock_vortex).parameters
+    mach, xs, xc, yc, kappa, mu, rc = _rows()["shock_vortex"]
+    assert sig["mach"].default == mach and sig["x_shock"].default == xs
+    assert tuple(sig["center"].default) == (xc, yc)
+    assert (sig["kappa"].default, sig["mu"].default, sig["rc"].default) == (kappa, mu, rc)
