@@ -124,7 +124,8 @@ typedef struct {
 } weno_mesh_info;
 
 /* Fills *p with the defaults: Euler, FP64, gamma 1.4, adv (1,1), eps 1e-6,
- * theta 3, rcond 1e-12, optimize 1, linear 0, n_threads 0, characteristic 0. */
+ * theta 3, rcond 1e-12, optimize 1, linear 0, n_threads 0, characteristic 0,
+ * inflow states and line all 0 (meshes with inflow faces must set them). */
 void weno_params_default(weno_params* p);
 
 /* Builds a mesh (Section 2; stencils of Sections 3.1 and 3.2).
