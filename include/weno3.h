@@ -63,7 +63,8 @@ typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_OUTFLOW = 1 } weno_bc_kind;
 typedef enum { WENO_EQN_SCALAR = 0, WENO_EQN_EULER = 1 } weno_eqn_kind;
 typedef enum { WENO_FP64 = 0, WENO_FP32C = 1 } weno_precision;
 
-/* Boundary description of one mesh instance. */
+/* Boundary description of one mesh instance.  A zero-initialised struct is a
+ * periodic box with no walls and no inflow sides; set bc, origin and extent. */
 typedef struct {
   int32_t bc;        /* weno_bc_kind: periodic in x and y, or outflow on every boundary face */
   double origin[2];  /* box origin: periodic box, or the sides named by `walls`              */
