@@ -491,7 +491,8 @@ def run_dmr(args):
     """The double Mach reflection of the paper's tests through the CUDA path: [0,4] x [0,1], Mach 10
     shock at 60 degrees through (1/6, 0), reflective bottom wall from x = 1/6, exact post-shock state on
     the left and on the bottom before x = 1/6, the exact moving shock on the top, outflow on the right;
-    t = 0.2, irregular quad and triangle meshes with h = 1/100, 1/200.  No exact solution: reports
+    t = 0.2, quad and triangle meshes with h = 1/100, 1/200 (irregular by default: --dmr-delta,
+    --dmr-diagonal).  No exact solution: reports
     completion, extrema, the incident shock's position on the top side against the exact
     1/6 + (1 + 20 t)/sqrt 3, the foot of the Mach stem on the wall and (optionally) a density image."""
     import torch
@@ -506,14 +507,16 @@ def run_dmr(args):
     for k in [int(x) for x in args.dmr_h.split(",")]:
         for kind in ("quad", "tri"):
             h = 1.0 / k
-            mi = S.tube_mesh(4 * k, k, (4.0, 1.0), kind, 0.1, seed=4, walls=(2,), wall_from=(0, 0, 1.0 / 6.0, 0),
-                             inflow=(0, 2, 3))
+            diag = None if args.dmr_diagonal == "random" else int(args.dmr_diagonal)
+            mi = S.tube_mesh(4 * k, k, (4.0, 1.0), kind, args.dmr_delta, seed=4, walls=(2,),
+                             wall_from=(0, 0, 1.0 / 6.0, 0), inflow=(0, 2, 3), diagonal=diag)
             mesh = Mesh.from_input(mi)
             W0 = S.cell_average(mi, d["f"], order=4)
             cen = mi.nodes[mi.padded_cells()[0]].mean(axis=1)
             top = cen[:, 1] > 1.0 - 0.75 * h
             bot = cen[:, 1] < 0.75 * h
-            row = {"mesh": f"irregular {kind}", "h": f"1/{k}", "cells": mi.n_cells, "inflow_faces": mesh.info.n_inflow}
+            row = {"mesh": kind, "delta": args.dmr_delta, "diagonal": args.dmr_diagonal, "h": f"1/{k}",
+                   "cells": mi.n_cells, "inflow_faces": mesh.info.n_inflow}
             precs = [p for p in args.precisions.split(",") if p == "fp32c" or k <= args.dmr_fp64_max]
             for ch in (False, True):
                 res = {}
@@ -611,6 +614,9 @@ def parse_args(argv=None):
     ap.add_argument("--dmr-h", default="100,200", help="1/h of the double Mach reflection meshes")
     ap.add_argument("--dmr-fp64-max", type=int, default=100, help="largest 1/h run in FP64 as well")
     ap.add_argument("--dmr-image-dir", default="", help="write density images (PNG) of the FP32C runs here")
+    ap.add_argument("--dmr-delta", type=float, default=0.1, help="node perturbation of the DMR meshes (0: regular)")
+    ap.add_argument("--dmr-diagonal", default="random", choices=["random", "0", "1"],
+                    help="diagonal along which the DMR triangle meshes split their quads")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     return ap.parse_args(argv)
 

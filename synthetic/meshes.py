@@ -151,8 +151,9 @@ def perturbed_quads(n: int, origin=(0.0, 0.0), extent=(1.0, 1.0), delta=0.1, see
     return pos, quads
 
 
-def split_quads(quads: np.ndarray, frac: float, seed: int):
-    """Split each quad with probability frac along a random diagonal.
+def split_quads(quads: np.ndarray, frac: float, seed: int, diagonal: int | None = None):
+    """Split each quad with probability frac along a random diagonal (diagonal = 0: always the
+    one through the quad's first and third nodes, 1: the other one).
 
     Returns (cell_ptr, cell_nodes) with cells in quad order; a split quad
     contributes its two triangles in place.
@@ -161,6 +162,8 @@ def split_quads(quads: np.ndarray, frac: float, seed: int):
     nq = quads.shape[0]
     split = rng.random(nq) < frac
     diag = rng.integers(0, 2, size=nq)
+    if diagonal is not None:
+        diag = np.full(nq, int(diagonal))
     a, b, c, d = quads.T
     sizes = np.where(split, 6, 4)
     ptr_q = np.concatenate([[0], np.cumsum(sizes)])
@@ -184,12 +187,12 @@ def split_quads(quads: np.ndarray, frac: float, seed: int):
     return cell_ptr, flat
 
 
-def _assemble(pos, quads, frac, seed, bc, origin, extent, name, meta):
+def _assemble(pos, quads, frac, seed, bc, origin, extent, name, meta, diagonal=None):
     if frac <= 0.0:
         cell_ptr = np.arange(0, 4 * quads.shape[0] + 1, 4, dtype=np.int64)
         cell_nodes = quads.reshape(-1).astype(np.int64)
     else:
-        cell_ptr, cell_nodes = split_quads(quads, frac, seed)
+        cell_ptr, cell_nodes = split_quads(quads, frac, seed, diagonal)
     return MeshInput(pos, cell_ptr, cell_nodes, bc, tuple(origin), tuple(extent), name, seed, dict(meta))
 
 
@@ -214,14 +217,15 @@ def _vortex_maps(L: float, a: float = 9.0 / 11.0):
 
 
 def tube_mesh(nx: int, ny: int, extent, kind="quad", delta=0.1, seed=0, walls=(), wall_from=(0.0, 0.0, 0.0, 0.0),
-              inflow=()):
+              inflow=(), diagonal=None):
     """Outflow box [0, Lx] x [0, Ly] of nx x ny perturbed quads (kind "quad"), all split into
-    triangles ("tri") or 30 % split ("mixed"); `walls`, `wall_from` and `inflow` name reflective and
-    inflow sides (see MeshInput)."""
+    triangles ("tri") or 30 % split ("mixed"), along random diagonals or the one `diagonal` names
+    (see split_quads); `walls`, `wall_from` and `inflow` name reflective and inflow sides (see
+    MeshInput)."""
     frac = {"quad": 0.0, "tri": 1.0, "mixed": 0.3}[kind]
     pos, quads = perturbed_quads(nx, (0.0, 0.0), tuple(extent), delta, seed, ny=ny)
     mi = _assemble(pos, quads, frac, seed, "outflow", (0.0, 0.0), tuple(extent), f"tube-{kind}-{nx}x{ny}",
-                   {"nx": nx, "ny": ny, "split": frac, "delta": delta})
+                   {"nx": nx, "ny": ny, "split": frac, "delta": delta, "diagonal": diagonal}, diagonal)
     mi.walls = tuple(walls)
     mi.wall_from = tuple(float(v) for v in wall_from)
     mi.inflow = tuple(inflow)
