@@ -276,29 +276,49 @@ def _cell_areas(mi):
     return 0.5 * np.abs((x * np.roll(y, -1, 1) - np.roll(x, -1, 1) * y).sum(1))  # padded vertex repeats add 0
 
 
+def _family(L, kind, delta):
+    return lambda n: __import__("synthetic").periodic_mesh(n, L, kind, delta, seed=0)
+
+
+# convergence families: mesh builder of n, initial / exact data, domain size.  "dw" = density wave on
+# [0,2]^2 and "vx" = isentropic vortex on [0,10]^2 (the accuracy tests of Section 4) on regular and
+# irregular (delta = 0.1) quads and split triangles; the benchmark's own families as well.
 ACC_FAMILIES = {
-    "densitywave-tri": (lambda n: __import__("synthetic").mesh_for_config(2, n=n, seed=0, kind="tri"), "density_wave"),
-    "vortex-lowq": (lambda n: __import__("synthetic").stretched_vortex_mesh(n, seed=0), "isentropic_vortex"),
+    "densitywave-tri": (lambda n: __import__("synthetic").mesh_for_config(2, n=n, seed=0, kind="tri"), "density_wave", 2.0),
+    "densitywave-quad": (lambda n: __import__("synthetic").mesh_for_config(1, n=n, seed=0), "density_wave", 2.0),
+    "vortex-lowq": (lambda n: __import__("synthetic").stretched_vortex_mesh(n, seed=0), "isentropic_vortex", 10.0),
+    "dw-quad-reg": (_family(2.0, "quad", 0.0), "density_wave", 2.0),
+    "dw-quad-irr": (_family(2.0, "quad", 0.1), "density_wave", 2.0),
+    "dw-tri-reg": (_family(2.0, "tri", 0.0), "density_wave", 2.0),
+    "dw-tri-irr": (_family(2.0, "tri", 0.1), "density_wave", 2.0),
+    "vx-quad-reg": (_family(10.0, "quad", 0.0), "isentropic_vortex", 10.0),
+    "vx-quad-irr": (_family(10.0, "quad", 0.1), "isentropic_vortex", 10.0),
+    "vx-tri-reg": (_family(10.0, "tri", 0.0), "isentropic_vortex", 10.0),
+    "vx-tri-irr": (_family(10.0, "tri", 0.1), "isentropic_vortex", 10.0),
 }
 
 
-def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic=False, optimize=True):
-    """One mesh of a convergence ladder run to t = T through the CUDA path: L1 / Linf of rho vs exact."""
+def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic=False, optimize=True, dt_h=None):
+    """One mesh of a convergence ladder run to t = T through the CUDA path: L1 / Linf of rho vs exact.
+
+    dt_h: fixed time step dt_h * h with h = L / n (the accuracy tests of Section 4 take dt = 0.3 h),
+    else the CFL step of the initial state.  l1 is the area-weighted mean of |rho - rho_exact|,
+    l1_int = sum |Omega_i| |rho_i - rho_exact_i| (the normalisation of the paper's tables)."""
     import torch
     import synthetic as S
     from paper_1712_08317_gb300.api import Mesh, Solver
-    mk, fname = ACC_FAMILIES[family]
+    mk, fname, L = ACC_FAMILIES[family]
     f = getattr(S, fname)
     mi = mk(n)
     mesh = Mesh.from_input(mi)
     W0 = S.cell_average(mi, f)
     ex = S.cell_average(mi, lambda x, y: f(x, y, T))
     area = _cell_areas(mi)
-    row = {"n": n, "cells": mi.n_cells}
+    row = {"n": n, "cells": mi.n_cells, "h": L / n}
     for prec in precisions:
         sol = Solver(mesh, eqn="euler", precision=prec, eps=eps, characteristic=characteristic, optimize=optimize)
         U, Ul = sol.to_device(W0)
-        dt0 = float(sol.max_dt(U, Ul, cfl)[0])
+        dt0 = dt_h * L / n if dt_h else float(sol.max_dt(U, Ul, cfl)[0])
         steps = int(np.ceil(T / dt0 - 1e-12))
         dt = T / steps
         t0 = time.perf_counter()
@@ -312,8 +332,8 @@ def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic
             row[prec] = {"steps": steps, "failed": str(exc).split(":")[0], "seconds": el}
             continue
         e = np.abs(sol.to_host(U, Ul)[0] - ex[0])
-        row[prec] = {"steps": steps, "l1": float((e * area).sum() / area.sum()), "linf": float(e.max()),
-                     "seconds": el}
+        row[prec] = {"steps": steps, "l1": float((e * area).sum() / area.sum()), "l1_int": float((e * area).sum()),
+                     "linf": float(e.max()), "seconds": el}
     if "l1" in row.get("fp32c", {}) and "l1" in row.get("fp64", {}):
         row["l1_fp32c_over_fp64"] = row["fp32c"]["l1"] / row["fp64"]["l1"]
     return row
@@ -559,8 +579,8 @@ def run_dmr(args):
 
 def run_accuracy(args):
     """Convergence ladders to t = 2 through the CUDA path: FP64 and FP32C, L1 / Linf of rho vs exact."""
-    ladders = {"densitywave-tri": [int(x) for x in args.ladder_dw.split(",")],
-               "vortex-lowq": [int(x) for x in args.ladder_vortex.split(",")]}
+    ladders = {name: [int(x) for x in (args.ladder_dw if fam[2] == 2.0 else args.ladder_vortex).split(",")]
+               for name, fam in ACC_FAMILIES.items()}
     T = 2.0
     out = {}
     for name, ladder in ladders.items():
@@ -569,7 +589,7 @@ def run_accuracy(args):
         rows = []
         for n in ladder:
             row = ladder_point(name, n, args.precisions.split(","), args.eps, args.cfl, T, args.characteristic,
-                               not args.raw_weights)
+                               not args.raw_weights, args.dt_h)
             rows.append(row)
             print(json.dumps({"family": name, **row}), flush=True)
         for prec in args.precisions.split(","):
@@ -580,7 +600,7 @@ def run_accuracy(args):
                 b[prec]["order_l1"] = float(np.log(a[prec]["l1"] / b[prec]["l1"]) / np.log(r))
                 b[prec]["order_linf"] = float(np.log(a[prec]["linf"] / b[prec]["linf"]) / np.log(r))
         out[name] = rows
-    print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "eps": args.eps,
+    print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "dt_h": args.dt_h, "eps": args.eps,
                       "characteristic": args.characteristic, "optimized_weights": not args.raw_weights}), flush=True)
 
 
@@ -603,6 +623,7 @@ def parse_args(argv=None):
     ap.add_argument("--ladder-vortex", default="40,80,160")
     ap.add_argument("--eps", type=float, default=1e-6, help="epsilon of the nonlinear weights (accuracy mode)")
     ap.add_argument("--cfl", type=float, default=0.5, help="CFL number of the accuracy runs")
+    ap.add_argument("--dt-h", type=float, default=None, help="accuracy mode: fixed dt = dt_h * h (Section 4: 0.3)")
     ap.add_argument("--precisions", default="fp64,fp32c")
     ap.add_argument("--characteristic", action="store_true", help="accuracy mode: characteristic-variable reconstruction")
     ap.add_argument("--raw-weights", action="store_true", help="accuracy mode: linear weights without the optimisation")

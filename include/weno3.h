@@ -92,7 +92,8 @@ typedef struct {
   double gas_gamma;   /* specific heat ratio of Eq. 1 (Euler)                              */
   double adv[2];      /* advection velocity (scalar)                                       */
   double eps;         /* epsilon of the nonlinear weights, Section 3.4 (not given: 1e-6)   */
-  double theta;       /* splitting parameter of Section 3.4 (3)                            */
+  double theta;       /* splitting parameter of Section 3.4 (3); must exceed 1, which keeps
+                         sigma- > 0 (weno_solver_create returns WENO_EINVAL otherwise)      */
   double rcond;       /* relative singular-value cut of the minimum-norm least squares that
                          stand for the zeta-regularised solves of Eqs. 12 and 15 (1e-12)   */
   int32_t optimize;   /* 1: optimised linear weights of Section 3.3 (default), 0: raw      */
@@ -281,6 +282,20 @@ int weno_solver_launch_config(weno_solver_t s, int32_t* cfg);
  * invalid.  on = 0 restores normal operation.  Step graphs are rebuilt.
  * WENO_EINVAL for solvers without such waits (FP64, scalar). */
 int weno_solver_debug_stall(weno_solver_t s, int32_t on);
+
+/* Measures the throughput of one SM pipe on the current device, as the peak
+ * against which the reconstruction kernels' arithmetic is placed (the paper
+ * has no counterpart; this is a measurement aid).  kind: 0 FP32 fused
+ * multiply-add (scalar instructions), 1 FP32 fused multiply-add (paired f32x2
+ * instructions), 2 FP64 fused multiply-add, 3 FP32 approximate reciprocal (the
+ * special-function pipe).  Launches 4 blocks of 256 threads per SM, each
+ * thread running 8 independent chains of `iters` dependent instructions, once
+ * to warm up and three times timed with CUDA events on cuda_stream; writes the
+ * operations of one launch to *ops (an FMA counts as one, a paired FMA as two)
+ * and the fastest launch's milliseconds to *ms.  Allocates and frees a small
+ * output buffer.  Errors: WENO_EINVAL (kind outside 0..3, iters <= 0, null
+ * outputs), WENO_ENOMEM, WENO_ECUDA.  Synchronising. */
+int weno_probe_peak(int32_t kind, int32_t iters, void* cuda_stream, double* ops, float* ms);
 
 void weno_solver_destroy(weno_solver_t s);
 

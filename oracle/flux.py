@@ -19,7 +19,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["hllc_flux", "upwind_flux", "euler_normal_flux", "pressure", "primitive_to_conservative"]
+__all__ = ["hllc_flux", "hllc_star", "upwind_flux", "euler_normal_flux", "pressure", "primitive_to_conservative"]
 
 
 def primitive_to_conservative(q, gamma):
@@ -50,11 +50,10 @@ def _x_flux(q, gamma):
     return np.stack([m, m * u + p, mt * u, (E + p) * u])
 
 
-def hllc_flux(WL, WR, nx, ny, gamma):
-    """HLLC flux through a face with unit normal (nx, ny), states (4, ...)."""
-    # T W: rotate momenta into (normal, tangential)
-    qL = np.stack([WL[0], WL[1] * nx + WL[2] * ny, -WL[1] * ny + WL[2] * nx, WL[3]])
-    qR = np.stack([WR[0], WR[1] * nx + WR[2] * ny, -WR[1] * ny + WR[2] * nx, WR[3]])
+def hllc_star(qL, qR, gamma):
+    """Wave speeds and star states of HLLC for states (4, ...) already in the face frame
+    (rho, rho u_n, rho u_t, E): dict with SL, SR, SS (contact speed), UsL, UsR (star states),
+    FL, FR (physical normal fluxes of qL, qR)."""
     rL, rR = qL[0], qR[0]
     uL, uR = qL[1] / rL, qR[1] / rR
     vL, vR = qL[2] / rL, qR[2] / rR
@@ -69,15 +68,24 @@ def hllc_flux(WL, WR, nx, ny, gamma):
     SL = np.minimum(uL - aL, ut - at)
     SR = np.maximum(uR + aR, ut + at)
     SS = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR))
-    FL = _x_flux(qL, gamma)
-    FR = _x_flux(qR, gamma)
 
     def star(q, r, u, v, p, S):
         f = r * (S - u) / (S - SS)
         return np.stack([f, f * SS, f * v, f * (q[3] / r + (SS - u) * (SS + p / (r * (S - u))))])
 
-    FsL = FL + SL * (star(qL, rL, uL, vL, pL, SL) - qL)
-    FsR = FR + SR * (star(qR, rR, uR, vR, pR, SR) - qR)
+    return {"SL": SL, "SR": SR, "SS": SS, "UsL": star(qL, rL, uL, vL, pL, SL),
+            "UsR": star(qR, rR, uR, vR, pR, SR), "FL": _x_flux(qL, gamma), "FR": _x_flux(qR, gamma)}
+
+
+def hllc_flux(WL, WR, nx, ny, gamma):
+    """HLLC flux through a face with unit normal (nx, ny), states (4, ...)."""
+    # T W: rotate momenta into (normal, tangential)
+    qL = np.stack([WL[0], WL[1] * nx + WL[2] * ny, -WL[1] * ny + WL[2] * nx, WL[3]])
+    qR = np.stack([WR[0], WR[1] * nx + WR[2] * ny, -WR[1] * ny + WR[2] * nx, WR[3]])
+    h = hllc_star(qL, qR, gamma)
+    SL, SR, SS, FL, FR = h["SL"], h["SR"], h["SS"], h["FL"], h["FR"]
+    FsL = FL + SL * (h["UsL"] - qL)
+    FsR = FR + SR * (h["UsR"] - qR)
     F = np.where(SL >= 0.0, FL, np.where(SS >= 0.0, FsL, np.where(SR > 0.0, FsR, FR)))
     # T^{-1}: rotate the momentum flux back
     return np.stack([F[0], F[1] * nx - F[2] * ny, F[1] * ny + F[2] * nx, F[3]])

@@ -28,12 +28,6 @@ numpy.linalg.pinv (singular values below rcond * sigma_max dropped).  The
 paper notes the two differ by O(zeta); the limit is what two independent
 implementations can agree on, since the B system is rank deficient.
 Reading of d_j: computed per Gauss point from that point's gamma.
-Reading of rounding-level weights: after the final solve, weights with
-|gamma_j| <= 1e-10 max_k |gamma_k| at that Gauss point are set to 0 and the
-rest rescaled to sum 1.  They are zero in exact arithmetic (e.g. a candidate
-made only of i0 and its outflow ghost, whose P^1_j is always W_0), but the
-solve leaves them at +-1e-15; since such a candidate has beta = 0, the
-nonlinear weights of Section 3.4 multiply that noise by 1/eps^2.
 """
 from __future__ import annotations
 
@@ -62,6 +56,12 @@ class Params:
     inflow_a: tuple | None = None
     inflow_b: tuple | None = None
     inflow_line: tuple = (1.0, 0.0, 0.0, 0.0)
+
+    def __post_init__(self):
+        # sigma- = sum (theta |gamma| - gamma) / 2 vanishes for theta = 1 when every gamma_j >= 0,
+        # and gamma- = gt- / sigma- is then undefined (Section 3.4 uses theta = 3)
+        if not self.theta > 1.0:
+            raise ValueError("the splitting of Section 3.4 needs theta > 1")
 
 
 @dataclass
@@ -124,16 +124,6 @@ def _d_weights(gamma, quad: bool):
         for j, k in ((4, 8), (8, 4), (5, 9), (9, 5), (6, 7), (7, 6)):
             d[..., j - 1] = 1.0 / np.maximum(np.maximum(1.0, a[..., j - 1]), a[..., k - 1])
     return d
-
-
-FLUSH_REL = 1e-10
-
-
-def flush_rounding_weights(gamma):
-    """Zero the weights at rounding level (<= 1e-10 of the largest per Gauss point), rescale to sum 1."""
-    big = np.abs(gamma).max(-1, keepdims=True)
-    g = np.where(np.abs(gamma) <= FLUSH_REL * big, 0.0, gamma)
-    return g / g.sum(-1, keepdims=True)
 
 
 def _group(mesh: OracleMesh, cells: np.ndarray, quad: bool, params: Params) -> GroupTables:
@@ -199,7 +189,6 @@ def _group(mesh: OracleMesh, cells: np.ndarray, quad: bool, params: Params) -> G
     else:
         eta_opt = eta
         gamma = gamma_raw
-    gamma = flush_rounding_weights(gamma)
     return GroupTables(cells=cells, M=M, G=G, area=mesh.area[cells], members=members, member_flip=member_flip,
                        grad_op=grad_op,
                        dG=dG, gamma=gamma, gamma_raw=gamma_raw, eta=eta_opt, eta_raw=eta, B=B,

@@ -14,7 +14,7 @@ OBJ = os.path.join(HERE, "_obj")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CXX_SOURCES = ["host_mesh.cpp", "host_lsq.cpp"]
-CU_SOURCES = ["solver.cu"]
+CU_SOURCES = ["solver.cu", "probe.cu"]
 
 
 def _nvcc() -> str:

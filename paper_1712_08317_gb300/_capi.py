@@ -61,6 +61,7 @@ SIGNATURES = {
     "weno_autotune": (C.c_int, [P, P, P, P]),
     "weno_solver_launch_config": (C.c_int, [P, P]),
     "weno_solver_debug_stall": (C.c_int, [P, C.c_int32]),
+    "weno_probe_peak": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
     "weno_solver_destroy": (None, [P]),
     "weno_last_error": (C.c_char_p, []),
 }

@@ -12,7 +12,20 @@ import numpy as np
 
 from . import _capi as capi
 
-__all__ = ["Mesh", "Solver", "split_fp32", "params_struct"]
+__all__ = ["Mesh", "Solver", "split_fp32", "params_struct", "probe_peak"]
+
+
+PROBE_KINDS = {"ffma": 0, "ffma2": 1, "dfma": 2, "rcp": 3}
+
+
+def probe_peak(kind: str, iters: int, stream=None):
+    """Measured throughput of one SM pipe (weno_probe_peak): (operations per second, ops, ms)."""
+    import torch
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream if stream is None else stream.cuda_stream)
+    ops = C.c_double()
+    ms = C.c_float()
+    capi.check(capi.load().weno_probe_peak(PROBE_KINDS[kind], int(iters), st, C.byref(ops), C.byref(ms)))
+    return ops.value / (ms.value * 1e-3), ops.value, ms.value
 
 
 def _ptr(a: np.ndarray):

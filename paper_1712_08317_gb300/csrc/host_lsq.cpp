@@ -216,7 +216,6 @@ void polygon_moments(const double v[4][2], int nv, const double c0[2], double s,
   if (area_out) *area_out = I0;
 }
 
-constexpr double kFlushRel = 1e-10;  // relative level of linear weights treated as zero
 constexpr double kGA = 0.78867513459481288225;  // (3 + sqrt 3) / 6, Eq. (5)
 constexpr double kGB = 0.21132486540518711775;  // (3 - sqrt 3) / 6
 
@@ -310,19 +309,7 @@ void cell_tables(const Mesh& m, const LsqParams& p, int64_t c, GroupTables& T, i
       eta[0] = 1.0 - sum;
       minnorm_cod(B, R, M, eta, 1, p.rcond, gam);
     }
-    // weights at rounding level are zero in exact arithmetic (e.g. a candidate
-    // made of i0 and its outflow ghost only, whose beta is always 0, so the
-    // nonlinear weights would scale their noise by 1/eps^2): drop them and
-    // rescale the rest to sum 1
-    double big = 0.0;
-    for (int j = 0; j < M; ++j) big = std::max(big, std::fabs(gam[j]));
-    double gsum = 0.0;
     for (int j = 0; j < M; ++j) {
-      if (std::fabs(gam[j]) <= kFlushRel * big) gam[j] = 0.0;
-      gsum += gam[j];
-    }
-    for (int j = 0; j < M; ++j) {
-      gam[j] /= gsum;
       T.gam[(g * M + j) * N + q] = gam[j];
       mopt = std::max(mopt, std::fabs(gam[j]));
     }

@@ -245,6 +245,27 @@ struct CandPairs {
   float2 gx[P], gy[P], b[P], be[P];
 };
 
+// Increment of one Gauss point as in gauss_increment below with every step of the nonlinear
+// weights in FP64 (IEEE division), from the n candidates' (beta, p = P^1_j(x_G) - W0, gamma+,
+// gamma-) in v[4n]: the fallback for weights outside the FP32 range.  Not inlined and looping at
+// run time, so the FP32 path keeps its registers; it runs only at Gauss points that need it.
+__device__ __noinline__ float nonlinear_increment_fp64(const float* __restrict__ v, int n, float sp, float sm,
+                                                      float eps_f) {
+  const double eps = eps_f;
+  double Ap = 0.0, Bp = 0.0, Am = 0.0, Bm = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double b = v[4 * j], p = v[4 * j + 1], gp = v[4 * j + 2], gn = v[4 * j + 3];
+    const double qp = gp * b, qn = gn * b;
+    const double dp = b * (1.0 + qp + qp * qp) + eps, dn = b * (1.0 + qn + qn * qn) + eps;
+    const double ap = gp / (dp * dp), an = gn / (dn * dn);
+    Ap += ap;
+    Bp += ap * p;
+    Am += an;
+    Bm += an * p;
+  }
+  return (float)((double)sp * (Bp / Ap) - (double)sm * (Bm / Am));
+}
+
 // Increment R(x_G) - W0 of one Gauss point (Section 3.4, FP32) from the
 // candidate pairs and the split linear weights gamma+ (gpos), gamma- (gneg)
 // with their sums sigma+- (sp, sm), which depend on geometry only and are
@@ -255,7 +276,8 @@ struct CandPairs {
 // The linear scheme is R - W0 = sum gamma_j p_j = sigma+ sum gamma+ p - sigma- sum gamma- p.
 template <int P>
 __device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const float2* gpos, const float2* gneg,
-                                                 float dx, float dy, float sp, float sm, int linear) {
+                                                 float dx, float dy, float sp, float sm, int linear, bool& redo) {
+  redo = false;
   const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy);
   if (linear) {
     float2 ap = f2(0.f, 0.f), an = f2(0.f, 0.f);
@@ -285,7 +307,31 @@ __device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const fl
       Am = __fadd2_rn(Am, an); Bm = __ffma2_rn(an, p, Bm);
     }
   }
-  return sp * (Bp.x + Bp.y) * rcp_approx(Ap.x + Ap.y) - sm * (Bm.x + Bm.y) * rcp_approx(Am.x + Am.y);
+  const float As = Ap.x + Ap.y, Bs = Bp.x + Bp.y, Ams = Am.x + Am.y, Bms = Bm.x + Bm.y;
+  // The FP32 weights are exact up to rounding while each group's sum of alpha stays in
+  // [kAlphaLo, kAlphaHi]: then (beta~ + eps)^2 of every candidate that matters is far from
+  // overflow and its reciprocal far from the flush-to-zero range.  Outside it (indicators of
+  // order 1e6 and more at strong jumps, or a tiny eps) the caller evaluates the Gauss point
+  // again with gauss_increment_fp64.
+  constexpr float kAlphaLo = 1e-30f, kAlphaHi = 1e30f;
+  redo = !(As >= kAlphaLo && As <= kAlphaHi && Ams >= kAlphaLo && Ams <= kAlphaHi);
+  return sp * Bs * rcp_approx(As) - sm * Bms * rcp_approx(Ams);
+}
+
+// gauss_increment with the nonlinear weights in FP64, whose range holds every finite FP32
+// beta; delta = alpha / sum alpha is the same function, so only rounding differs.
+template <int P>
+__device__ __forceinline__ float gauss_increment_fp64(const CandPairs<P>& c, const float2* gpos, const float2* gneg,
+                                                      float dx, float dy, float sp, float sm, float eps) {
+  const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy);
+  float v[8 * P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const float2 p = __ffma2_rn(c.gx[k], dx2, __fmul2_rn(c.gy[k], dy2));
+    v[8 * k + 0] = c.b[k].x; v[8 * k + 1] = p.x; v[8 * k + 2] = gpos[k].x; v[8 * k + 3] = gneg[k].x;
+    v[8 * k + 4] = c.b[k].y; v[8 * k + 5] = p.y; v[8 * k + 6] = gpos[k].y; v[8 * k + 7] = gneg[k].y;
+  }
+  return nonlinear_increment_fp64(v, 2 * P, sp, sm, eps);
 }
 
 // Candidate gradients and smoothness indicators of one (cell, variable), as
@@ -343,10 +389,9 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
     CandPairs<P> cp;
     cell_gradients<NV, M, false>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
     float* out = Wg + (gbase + q * G) * NV + v;
-#pragma unroll 1
-    for (int g = 0; g < G; ++g) {
-      const float4 d = __ldg(dgs + (int64_t)g * pitch + q);
-      float2 gp[P], gn[P];
+    // (x_G - c0, sigma+-) and the split weights of Gauss point g
+    auto tables = [&](int g, float4& d, float2* gp, float2* gn) {
+      d = __ldg(dgs + (int64_t)g * pitch + q);
 #pragma unroll
       for (int k = 0; k < M4; ++k) {
         const float4 x = __ldg(gpm4 + (int64_t)(g * 2 * M4 + k) * pitch + q);
@@ -359,8 +404,25 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
         gp[P - 1] = f2(e.x, 0.f);
         gn[P - 1] = f2(e.y, 0.f);
       }
-      const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
+    };
+    uint32_t redo = 0u;  // Gauss points whose weights left the FP32 range
+#pragma unroll 1
+    for (int g = 0; g < G; ++g) {
+      float4 d;
+      float2 gp[P], gn[P];
+      tables(g, d, gp, gn);
+      bool r;
+      const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, r);
+      redo |= (uint32_t)r << g;
       out[(int64_t)g * NV] = w0 + (l0 + incr);
+    }
+#pragma unroll 1
+    for (int g = 0; redo != 0u; ++g, redo >>= 1) {
+      if (!(redo & 1u)) continue;
+      float4 d;
+      float2 gp[P], gn[P];
+      tables(g, d, gp, gn);
+      out[(int64_t)g * NV] = w0 + (l0 + gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps));
     }
   }
 }
@@ -503,10 +565,8 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
       const float2* sg1 = reinterpret_cast<const float2*>(base + L::GPM + L::DGS);
       const int cl = tid >> 2;
       float* out = Wg + (gbase + q * G) * 4 + v;
-#pragma unroll 1
-      for (int g = 0; g < G; ++g) {
-        const float4 d = sds[g * L::TILE + cl];
-        float2 gp[P], gn[P];
+      auto tables = [&](int g, float4& d, float2* gp, float2* gn) {
+        d = sds[g * L::TILE + cl];
 #pragma unroll
         for (int k = 0; k < L::M4; ++k) {
           const float4 x = sgp[(g * 2 * L::M4 + k) * L::TILE + cl];
@@ -519,8 +579,25 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
           gp[P - 1] = f2(e.x, 0.f);
           gn[P - 1] = f2(e.y, 0.f);
         }
-        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
+      };
+      uint32_t redo = 0u;  // Gauss points whose weights left the FP32 range
+#pragma unroll 1
+      for (int g = 0; g < G; ++g) {
+        float4 d;
+        float2 gp[P], gn[P];
+        tables(g, d, gp, gn);
+        bool r;
+        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, r);
+        redo |= (uint32_t)r << g;
         out[(int64_t)g * 4] = w0 + (l0 + incr);
+      }
+#pragma unroll 1
+      for (int g = 0; redo != 0u; ++g, redo >>= 1) {
+        if (!(redo & 1u)) continue;
+        float4 d;
+        float2 gp[P], gn[P];
+        tables(g, d, gp, gn);
+        out[(int64_t)g * 4] = w0 + (l0 + gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps));
       }
     }
     __syncthreads();  // the buffer is free for the copy issued in the next iteration
@@ -960,11 +1037,7 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
         cp.b[p] = f2(b[2 * p], b[2 * p + 1]);
         cp.be[p] = __fadd2_rn(cp.b[p], f2(eps, eps));
       }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int g = 2 * k + h;
-        const float4 d = h ? d1 : d0;
-        float2 gp[P], gn[P];
+      auto weights = [&](int g, float2* gp, float2* gn) {
 #pragma unroll
         for (int kk = 0; kk < L::M4; ++kk) {
           const float4 x = sgp[(g * 2 * L::M4 + kk) * L::TILE + cl];
@@ -977,9 +1050,32 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
           gp[P - 1] = f2(e.x, 0.f);
           gn[P - 1] = f2(e.y, 0.f);
         }
-        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear);
-        const float dWl = lane_sum4(Rr, incr, base);
-        if (act) Wg[(gbase + q * G + g) * 4 + l] = w0 + (l0 + dWl);
+      };
+      float incr[2];
+      bool redo[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 d = h ? d1 : d0;
+        float2 gp[P], gn[P];
+        weights(2 * k + h, gp, gn);
+        incr[h] = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, redo[h]);
+      }
+      // weights outside the FP32 range: those lanes redo their points in FP64 before the
+      // (converged) back-projection
+      if (redo[0] || redo[1]) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          if (!redo[h]) continue;
+          const float4 d = h ? d1 : d0;
+          float2 gp[P], gn[P];
+          weights(2 * k + h, gp, gn);
+          incr[h] = gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float dWl = lane_sum4(Rr, incr[h], base);
+        if (act) Wg[(gbase + q * G + 2 * k + h) * 4 + l] = w0 + (l0 + dWl);
       }
     }
     __syncthreads();  // the buffer is free for the next tile's copy

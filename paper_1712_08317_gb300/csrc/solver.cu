@@ -16,6 +16,10 @@
 #include "kernels.cuh"
 #include "weno3.h"
 
+namespace weno {
+int set_error(int code, const std::string& msg);
+}
+
 using weno::GroupTables;
 using weno::Mesh;
 
@@ -27,6 +31,12 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+
+}  // namespace
+
+int weno::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+namespace {
 
 #define CK(call)                                                                                 \
   do {                                                                                           \
@@ -656,8 +666,10 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   const weno_params& p = *params;
   if (p.eqn != WENO_EQN_SCALAR && p.eqn != WENO_EQN_EULER) return fail(WENO_EINVAL, "unknown equation");
   if (p.precision != WENO_FP64 && p.precision != WENO_FP32C) return fail(WENO_EINVAL, "unknown precision");
-  if (!(p.eps > 0) || !(p.theta >= 1) || (p.eqn == WENO_EQN_EULER && !(p.gas_gamma > 1)))
-    return fail(WENO_EINVAL, "parameters out of range (eps > 0, theta >= 1, gamma > 1)");
+  // theta > 1 keeps sigma- = sum (theta |gamma| - gamma) / 2 > 0 (Section 3.4); at theta = 1 a Gauss
+  // point whose linear weights are all >= 0 has sigma- = 0 and gamma- = 0 / 0
+  if (!(p.eps > 0) || !(p.theta > 1) || (p.eqn == WENO_EQN_EULER && !(p.gas_gamma > 1)))
+    return fail(WENO_EINVAL, "parameters out of range (eps > 0, theta > 1, gamma > 1)");
   if (p.characteristic && p.eqn != WENO_EQN_EULER)
     return fail(WENO_EINVAL, "characteristic variables are defined for the Euler equations only");
   const bool walls = std::any_of(mesh->m.fwall.begin(), mesh->m.fwall.end(), [](int8_t w) { return w >= 0; });

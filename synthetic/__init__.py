@@ -8,14 +8,14 @@ fluxes or time stepping.  Every random draw uses numpy's PCG64 with an
 explicit seed, so the same call gives the same bytes on every machine.
 """
 from .meshes import (MeshInput, quad_grid, perturbed_quads, split_quads, stretched_vortex_mesh,
-                     mesh_for_config, batch_instances, instance_mesh, tube_mesh)
+                     mesh_for_config, batch_instances, instance_mesh, tube_mesh, periodic_mesh)
 from .flows import (density_wave, isentropic_vortex, scalar_wave, four_quadrant_states,
                     cell_average, four_quadrant_average, euler_prim_to_cons, riemann_exact, shock_tube, shock_vortex,
                     moving_shock, double_mach)
 
 __all__ = [
     "MeshInput", "quad_grid", "perturbed_quads", "split_quads", "stretched_vortex_mesh",
-    "mesh_for_config", "batch_instances", "instance_mesh", "tube_mesh", "density_wave", "isentropic_vortex", "scalar_wave",
+    "mesh_for_config", "batch_instances", "instance_mesh", "tube_mesh", "periodic_mesh", "density_wave", "isentropic_vortex", "scalar_wave",
     "four_quadrant_states", "cell_average", "four_quadrant_average", "euler_prim_to_cons", "riemann_exact",
     "shock_tube", "shock_vortex", "moving_shock", "double_mach",
 ]

@@ -478,3 +478,26 @@ def test_batched_instances_with_inflow_keep_their_own_time():
     assert np.array_equal(out[:, a.n_cells:], singles[1].to_host(*states[1]))
     t = big.get_time()
     assert t[0] == dts[0] + dts[0] + dts[0] + dts[0] and t[1] == dts[1] + dts[1] + dts[1] + dts[1]
+
+
+@pytest.mark.parametrize("shape,size", [("ramp", 1e5), ("ramp", 1e7), ("step", 1e4), ("step", 1e5)])
+def test_fp32c_weights_stay_finite_at_huge_indicators(shape, size):
+    """Section 3.4's alpha = gamma / (beta~ + eps)^2 with beta~ ~ gamma^2 beta^3: a steep pressure
+    ramp makes every candidate's beta ~ 1e8-1e12, so (beta~ + eps)^2 overflows FP32 and every alpha
+    of a group flushes to zero; a strong step puts such indicators next to smooth candidates.  The
+    FP32C path must still match the oracle (FP64) to FP32 accuracy, with no NaN."""
+    mi = S.mesh_for_config(3, n=14, seed=2, kind="mixed")
+    om = OracleMesh.from_input(mi)
+    cen = om.centroid
+    if shape == "ramp":
+        p = 1.0 + size * (cen[:, 0] + 0.3 * cen[:, 1])
+    else:
+        p = np.where(cen[:, 0] + 0.3 * cen[:, 1] < 0.55, size, 1.0)
+    W = S.euler_prim_to_cons(np.ones_like(p), 0.0 * p, 0.0 * p, p, 1.4)
+    ref = OracleSolver(om, Params()).residual(W)
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c")
+    U, Ul = sol.to_device(W)
+    Rd = sol.residual(U, Ul)
+    assert bool(torch.isfinite(Rd).all())
+    sol.check()
+    assert _rel(sol.to_host(Rd), ref) < 2e-3

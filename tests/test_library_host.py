@@ -165,3 +165,17 @@ def test_inflow_options_are_validated(lib):
         with pytest.raises(_capi.WenoError) as e:
             Mesh(mi.nodes, mi.cell_ptr, mi.cell_nodes, bc, (0.0, 0.0), (1.0, 1.0), inflow=inflow, wall_from=wall_from)
         assert e.value.code == _capi.WENO_EINVAL
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_solver_create_rejects_theta_at_most_one(lib, theta):
+    """The splitting of Section 3.4 needs theta > 1 (sigma- > 0); the check precedes any CUDA call."""
+    from paper_1712_08317_gb300 import _capi
+    from paper_1712_08317_gb300.api import Mesh, params_struct
+    m = Mesh.from_input(S.mesh_for_config(1, n=6, seed=0))
+    p = params_struct(theta=theta)
+    h = ctypes.c_void_p()
+    assert lib.weno_solver_create(m._h, ctypes.byref(p), None, ctypes.byref(h)) == _capi.WENO_EINVAL
+    assert b"theta" in lib.weno_last_error()
+    with pytest.raises(ValueError):
+        Params(theta=theta)

@@ -4,7 +4,7 @@ import pytest
 
 import synthetic as S
 from oracle import OracleMesh, OracleSolver, Params
-from oracle.flux import euler_normal_flux, hllc_flux, upwind_flux
+from oracle.flux import euler_normal_flux, hllc_flux, hllc_star, upwind_flux
 
 GAM = 1.4
 
@@ -55,6 +55,65 @@ def test_hllc_rotational_invariance_and_mirror_symmetry():
     assert np.allclose(Fr, rot(F), rtol=1e-12, atol=1e-12)
     # swapping the sides and the normal reverses the flux
     assert np.allclose(hllc_flux(WR, WL, -nx, -ny, GAM), -F, rtol=1e-12, atol=1e-12)
+
+
+def _star_cases(n=400, seed=7):
+    """Random subsonic face-frame states (S_L < 0 < S_R) whose contact speed differs from both
+    normal velocities, the general case of the star region."""
+    rng = np.random.default_rng(seed)
+    qL = _W(rng.uniform(0.2, 2, n), rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(0.1, 3, n))
+    qR = _W(rng.uniform(0.2, 2, n), rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(0.1, 3, n))
+    h = hllc_star(qL, qR, GAM)
+    uL, uR = qL[1] / qL[0], qR[1] / qR[0]
+    sel = (h["SL"] < 0) & (h["SR"] > 0) & (np.abs(h["SS"] - uL) > 1e-2) & (np.abs(h["SS"] - uR) > 1e-2)
+    assert sel.sum() > n // 2
+    return qL[:, sel], qR[:, sel], {k: v[..., sel] for k, v in h.items()}
+
+
+def test_hllc_star_states_satisfy_the_integral_consistency_condition():
+    """Toro ch. 10: over the Riemann fan [S_L t, S_R t] the star states integrate to the HLL
+    average, (S* - S_L) U*_L + (S_R - S*) U*_R = S_R U_R - S_L U_L - (F_R - F_L), and the star
+    fluxes F*_K = F_K + S_K (U*_K - U_K) jump by S* (U*_R - U*_L) across the contact."""
+    qL, qR, h = _star_cases()
+    SL, SR, SS, UL, UR = h["SL"], h["SR"], h["SS"], h["UsL"], h["UsR"]
+    lhs = (SS - SL) * UL + (SR - SS) * UR
+    rhs = SR * qR - SL * qL - (h["FR"] - h["FL"])
+    assert np.abs(lhs - rhs).max() <= 1e-13 * np.abs(rhs).max()
+    FsL = h["FL"] + SL * (UL - qL)
+    FsR = h["FR"] + SR * (UR - qR)
+    assert np.abs(FsR - (FsL + SS * (UR - UL))).max() <= 1e-13 * np.abs(FsR).max()
+
+
+def test_hllc_star_states_obey_rankine_hugoniot_with_one_star_pressure():
+    """Across each outer wave the jump obeys Rankine-Hugoniot, with the star state moving at the
+    contact speed, keeping its side's tangential velocity and carrying the pressure
+    p* = p_K + rho_K (S_K - u_K)(S* - u_K), the same on both sides (this fixes S*; a sign slip in
+    its numerator or in the star energy breaks one of these equalities)."""
+    qL, qR, h = _star_cases(seed=8)
+    SS = h["SS"]
+    pstar = []
+    for q, S, U, F in ((qL, h["SL"], h["UsL"], h["FL"]), (qR, h["SR"], h["UsR"], h["FR"])):
+        r, u, v = q[0], q[1] / q[0], q[2] / q[0]
+        p = (GAM - 1.0) * (q[3] - 0.5 * r * (u * u + v * v))
+        ps = p + r * (S - u) * (SS - u)
+        pstar.append(ps)
+        assert np.allclose(U[1] / U[0], SS, rtol=1e-13, atol=1e-13)        # u* = S*
+        assert np.allclose(U[2] / U[0], v, rtol=1e-13, atol=1e-13)         # tangential velocity kept
+        phys = np.stack([U[0] * SS, U[0] * SS * SS + ps, U[2] * SS, (U[3] + ps) * SS])
+        jump = F + S * (U - q)                                             # F*_K from Rankine-Hugoniot
+        assert np.abs(jump - phys).max() <= 1e-13 * np.abs(phys).max()
+    assert np.allclose(pstar[0], pstar[1], rtol=1e-13)
+
+
+def test_hllc_flux_takes_the_star_flux_on_the_side_of_the_contact():
+    """In the face frame (n = (1, 0)) the flux at x/t = 0 is F*_L when S* >= 0 and F*_R otherwise."""
+    qL, qR, h = _star_cases(seed=9)
+    F = hllc_flux(qL, qR, 1.0, 0.0, GAM)
+    FsL = h["FL"] + h["SL"] * (h["UsL"] - qL)
+    FsR = h["FR"] + h["SR"] * (h["UsR"] - qR)
+    want = np.where(h["SS"] >= 0, FsL, FsR)
+    assert (h["SS"] >= 0).any() and (h["SS"] < 0).any()
+    assert np.abs(F - want).max() <= 1e-14 * np.abs(want).max()
 
 
 def test_upwind_flux():

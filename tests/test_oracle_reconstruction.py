@@ -163,3 +163,26 @@ def test_zeta_regularised_solves_converge_to_the_minimum_norm_solution(outflow_c
                  for z in (1e-5, 1e-6, 1e-7)]
             assert d[2] < d[1] < d[0] < 1e-2
             assert 5.0 < d[0] / d[1] < 20.0 and 5.0 < d[1] / d[2] < 20.0   # linear in zeta
+
+
+@pytest.mark.parametrize("case", ["outflow-mixed", "periodic-tri", "vortex", "walls-tri", "raw-mixed"])
+def test_no_linear_weight_sits_at_rounding_level(case):
+    """With mirror-image stencils at boundaries every candidate carries a genuine linear weight:
+    none lies at the rounding level of the solve (|gamma_j| ~ 1e-16 max|gamma|), where the
+    nonlinear weights of Section 3.4 would scale solver noise by 1/eps^2 and two correct
+    implementations could disagree.  The smallest weights on these families are ~1e-7 relative."""
+    prm = Params()
+    if case == "outflow-mixed":
+        mi = S.mesh_for_config(3, n=9, seed=5, kind="mixed")
+    elif case == "periodic-tri":
+        mi = S.mesh_for_config(2, n=12, seed=0, kind="tri")
+    elif case == "vortex":
+        mi = S.stretched_vortex_mesh(12, seed=0)
+    elif case == "walls-tri":
+        mi = S.tube_mesh(12, 6, (1.0, 0.5), "tri", 0.1, seed=1, walls=(2, 3))
+    else:
+        mi = S.mesh_for_config(3, n=9, seed=5, kind="mixed")
+        prm = Params(optimize=False)
+    for t in precompute(OracleMesh.from_input(mi), prm):
+        rel = np.abs(t.gamma) / np.abs(t.gamma).max(-1, keepdims=True)
+        assert rel.min() > 1e-9, (case, t.M, rel.min())
