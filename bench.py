@@ -29,11 +29,11 @@ if ROOT not in sys.path:
 METRIC = "WENO3 cell-updates/s (×RK stages) on 1 GB300, FP32+batched vs FP64 at stated L1 error"
 UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
-FP32_LANES_PER_SM = 128        # Blackwell SM: 4 partitions x 32 FP32 lanes, one FMA per lane per clock
-# DRAM bytes per cell of one reconstruction launch (ncu dram__bytes_read.sum + dram__bytes_write.sum
-# of k_reconstruct_tma on the 637k-cell mesh of the same family, divided by its cells; the command is in
-# profiles/k_reconstruct_tma_n700_fp32c.md).  Set to None whenever that kernel changes until re-measured.
-K1_TRAFFIC_PER_CELL = {"quad": 1305.7, "tri": 850.3}
+# DRAM bytes per cell of one reconstruction launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of
+# k_reconstruct_tma on the 637k-cell mesh of the benchmark family (n = 700), divided by its cells of
+# each type.  They describe the kernel source they were captured on (SHA-256 of csrc/kernels.cuh);
+# for any other source the bench line reports traffic null.
+K1_TRAFFIC = {"kernels_cuh_sha256": None, "quad": None, "tri": None}
 WORKLOAD_N = 1754
 
 
@@ -57,17 +57,54 @@ def hbm_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples of one GPU while running."""
+    """SM clock and throttle-reason samples of one GPU while running: NVML (read-only queries through
+    ctypes) every 2 ms from a thread, so short timed regions still get many samples; nvidia-smi
+    (100 ms) if NVML cannot be loaded."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReasons bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, bus_id):
         self.bus_id = bus_id
         self.proc = None
+        self.thread = None
+        self.nvml = None
         self.path = os.path.join("/tmp", f"weno_clocks_{os.getpid()}.csv")
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                if lib.nvmlDeviceGetHandleByPciBusId_v2(bus_id.encode(), ctypes.byref(h)) == 0:
+                    self.nvml, self.handle, self.ct = lib, h, ctypes
+                    self.reasons_fn = (getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+                                       or getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None))
+        except Exception:
+            self.nvml = None
+
+    def _poll(self):
+        ct, lib, h = self.ct, self.nvml, self.handle
+        clk, mx, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        while not self.done:
+            if lib.nvmlDeviceGetClockInfo(h, 1, ct.byref(clk)) == 0:        # NVML_CLOCK_SM
+                self.sm.append(clk.value)
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ct.byref(mx)) == 0:
+                self.smax.append(mx.value)
+            if self.reasons_fn is not None and self.reasons_fn(h, ct.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            time.sleep(0.002)
 
     def start(self):
+        self.sm, self.smax, self.reasons, self.done = [], [], set(), False
+        if self.nvml is not None:
+            import threading
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.bus_id}", f"--query-gpu={self.FIELDS}",
@@ -77,47 +114,117 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
+        if self.thread is not None:
+            self.done = True
+            self.thread.join()
+            sm, smax, reasons = self.sm, self.smax, self.reasons
+            src = "nvml 2 ms"
+        elif self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        self.proc.terminate()
-        self.proc.wait()
-        self.f.close()
-        sm, smax, reasons = [], [], set()
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
-                                 parts[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        os.remove(self.path)
+        else:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+            sm, smax, reasons = [], [], set()
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                     parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+            os.remove(self.path)
+            src = "nvidia-smi 100 ms"
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": src}
 
 
-def oracle_sample(seconds=10.0, n=60, steps=None):
-    """Time the FP64 CPU oracle on a bounded sample of the workload (same mesh family at size n)."""
+def _oracle_worker(n, seconds, barrier, out):
+    """One oracle replica: set up the mesh family at size n, wait for the others, then step for
+    `seconds`; puts (cells, steps, elapsed) on `out`."""
     import synthetic as S
     from oracle import OracleMesh, OracleSolver, Params
     mi = S.stretched_vortex_mesh(n, seed=0)
     sol = OracleSolver(OracleMesh.from_input(mi), Params())
     W = S.cell_average(mi, S.isentropic_vortex)
     dt = sol.max_dt(W, 0.5)
+    W = sol.rk3_step(W, dt)  # first step outside the timed loop
+    if barrier is not None:
+        barrier.wait()
     done = 0
     t0 = time.perf_counter()
-    while (steps is None and time.perf_counter() - t0 < seconds) or (steps is not None and done < steps):
+    while time.perf_counter() - t0 < seconds:
         W = sol.rk3_step(W, dt)
         done += 1
-    el = time.perf_counter() - t0
-    return {"value": mi.n_cells * 3 * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} RK3 steps of the numpy FP64 oracle on the same mesh family at n={n} "
-                      f"({mi.n_cells} cells), {el:.1f} s, single-threaded elementwise numpy"}, mi.n_cells, el, done
+    out.put((mi.n_cells, done, time.perf_counter() - t0))
+
+
+def cpu_model():
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_sample(seconds=10.0, n=60, cores=1):
+    """Time the FP64 CPU oracle (numpy, as it stands) on a bounded sample of the workload: the same
+    mesh family at size n, `cores` independent replicas in spawn-started processes (one BLAS thread
+    each) stepping concurrently for `seconds`; whole-job cell-updates/s = all replicas' cell-updates
+    over the longest replica's time."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        out = ctx.Queue()
+        barrier = ctx.Barrier(cores)
+        procs = [ctx.Process(target=_oracle_worker, args=(n, seconds, barrier, out)) for _ in range(cores)]
+        for p in procs:
+            p.start()
+        import queue
+        res = []
+        deadline = time.perf_counter() + seconds + 600.0
+        while len(res) < cores:
+            try:
+                res.append(out.get(timeout=1.0))
+            except queue.Empty:
+                if time.perf_counter() > deadline or any(p.exitcode not in (None, 0) for p in procs):
+                    for p in procs:
+                        if p.is_alive():
+                            p.terminate()
+                    raise RuntimeError("an oracle replica failed or timed out")
+        for p in procs:
+            p.join()
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    cells = res[0][0]
+    total = sum(c * 3 * d for c, d, _ in res)
+    el = max(e for _, _, e in res)
+    steps = sum(d for _, d, _ in res)
+    return {"value": total / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} replica(s) of the numpy FP64 oracle, {steps} RK3 steps in all on the same mesh "
+                      f"family at n={n} ({cells} cells each), {el:.1f} s, one thread per replica",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def dist_setup(backend=None):
@@ -236,6 +343,36 @@ def run_batched(args, torch, stream, dist=None, ws=1):
             "nonphysical_riemann_instances": int(sum(1 for d, b in zip(descs, bad) if b and d["data"] == "riemann"))}
 
 
+def k1_traffic(nQ, nT):
+    """ncu DRAM bytes of one reconstruction pass, or None if the kernel source changed since the capture."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1712_08317_gb300", "csrc", "kernels.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if K1_TRAFFIC["kernels_cuh_sha256"] != sha or K1_TRAFFIC["quad"] is None:
+        return None
+    return nQ * K1_TRAFFIC["quad"] + nT * K1_TRAFFIC["tri"]
+
+
+def measure_peaks():
+    """Measured pipe throughputs of this GPU (weno_probe_peak), in Top/s with an FMA counted as one
+    operation: FP32 FMA (the better of scalar and paired instructions), FP64 FMA, MUFU reciprocal."""
+    from paper_1712_08317_gb300.api import probe_peak
+    out = {}
+    for kind, iters in (("ffma", 20000), ("ffma2", 10000), ("dfma", 400), ("rcp", 8000)):
+        out[kind] = probe_peak(kind, iters)[0] / 1e12
+    out["fp32_fma"] = max(out["ffma"], out["ffma2"])
+    return out
+
+
+def step_bytes(nQ, nT):
+    """Algorithmic HBM bytes of one RK stage of the whole residual + update (FP32C, Euler), per the
+    minimum model: state hi / lo read and written with the stage buffer (96 B), candidate gradient
+    operators (M x 16 B), Gauss offsets (G x 8 B), linear weights (G x M x 4 B), stencil ids and
+    1/|Omega| (4 M + 4 B), face data (40 B per quad, 30 B per triangle): 828 B per quad, 574 B per
+    triangle."""
+    return nQ * 828 + nT * 574
+
+
 def k1_bytes(nQ, nT, nv, esz, comp):
     """Algorithmic bytes of one reconstruction pass (tables + one state read + Gauss-value writes)."""
     def per(M, G):
@@ -258,6 +395,17 @@ def k1_ops(nQ, nT, nv=4):
     return nQ * per(12, 8) + nT * per(9, 6)
 
 
+def k1_ops_fp64(nQ, nT, nv=4):
+    """Algorithmic FP64 operations (an FMA or a division counts one) of one FP64 reconstruction pass,
+    which splits the linear weights at every Gauss point: per (cell, variable) 1 per stencil slot and
+    8 per candidate; per Gauss point and candidate 4 (split sums) + 25 (split weights 5, P^1_j(x_G) -
+    W0 2, per sign q, beta~ + eps (3), its square, alpha = gamma / square, sums 2: 9); per Gauss
+    point 6 (two reciprocals of sigma, the combination)."""
+    def per(M, G):
+        return nv * (9 * M + G * (29 * M + 6))
+    return nQ * per(12, 8) + nT * per(9, 6)
+
+
 def k1_ops_char(nQ, nT):
     """Algorithmic FP32 operations (FMA = 1) of one characteristic-variable reconstruction pass:
     per (cell, field) 3 per stencil slot (Delta W); per face the Roe frame (60), the projection of
@@ -276,8 +424,8 @@ def _cell_areas(mi):
     return 0.5 * np.abs((x * np.roll(y, -1, 1) - np.roll(x, -1, 1) * y).sum(1))  # padded vertex repeats add 0
 
 
-def _family(L, kind, delta):
-    return lambda n: __import__("synthetic").periodic_mesh(n, L, kind, delta, seed=0)
+def _family(L, kind, delta, diagonal=None):
+    return lambda n: __import__("synthetic").periodic_mesh(n, L, kind, delta, seed=0, diagonal=diagonal)
 
 
 # convergence families: mesh builder of n, initial / exact data, domain size.  "dw" = density wave on
@@ -289,16 +437,21 @@ ACC_FAMILIES = {
     "vortex-lowq": (lambda n: __import__("synthetic").stretched_vortex_mesh(n, seed=0), "isentropic_vortex", 10.0),
     "dw-quad-reg": (_family(2.0, "quad", 0.0), "density_wave", 2.0),
     "dw-quad-irr": (_family(2.0, "quad", 0.1), "density_wave", 2.0),
-    "dw-tri-reg": (_family(2.0, "tri", 0.0), "density_wave", 2.0),
+    "dw-tri-reg": (_family(2.0, "tri", 0.0, 0), "density_wave", 2.0),
+    "dw-tri-reg-x": (_family(2.0, "tri", 0.0), "density_wave", 2.0),
     "dw-tri-irr": (_family(2.0, "tri", 0.1), "density_wave", 2.0),
     "vx-quad-reg": (_family(10.0, "quad", 0.0), "isentropic_vortex", 10.0),
     "vx-quad-irr": (_family(10.0, "quad", 0.1), "isentropic_vortex", 10.0),
-    "vx-tri-reg": (_family(10.0, "tri", 0.0), "isentropic_vortex", 10.0),
+    "vx-tri-reg": (_family(10.0, "tri", 0.0, 0), "isentropic_vortex", 10.0),
+    "vx-tri-reg-x": (_family(10.0, "tri", 0.0), "isentropic_vortex", 10.0),
     "vx-tri-irr": (_family(10.0, "tri", 0.1), "isentropic_vortex", 10.0),
+    # scalar advection u_t + u_x + u_y = 0 on the config-1 perturbed quads
+    "config1-scalar": (lambda n: __import__("synthetic").mesh_for_config(1, n=n, seed=0), "scalar_wave", 2.0),
 }
+SCALAR_FAMILIES = {"config1-scalar"}
 
 
-def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic=False, optimize=True, dt_h=None):
+def ladder_point(family, n, precisions, eps=1e-3, cfl=0.5, T=2.0, characteristic=False, optimize=True, dt_h=None):
     """One mesh of a convergence ladder run to t = T through the CUDA path: L1 / Linf of rho vs exact.
 
     dt_h: fixed time step dt_h * h with h = L / n (the accuracy tests of Section 4 take dt = 0.3 h),
@@ -315,8 +468,10 @@ def ladder_point(family, n, precisions, eps=1e-6, cfl=0.5, T=2.0, characteristic
     ex = S.cell_average(mi, lambda x, y: f(x, y, T))
     area = _cell_areas(mi)
     row = {"n": n, "cells": mi.n_cells, "h": L / n}
+    eqn = "scalar" if family in SCALAR_FAMILIES else "euler"
     for prec in precisions:
-        sol = Solver(mesh, eqn="euler", precision=prec, eps=eps, characteristic=characteristic, optimize=optimize)
+        sol = Solver(mesh, eqn=eqn, precision=prec, eps=eps, characteristic=characteristic and eqn == "euler",
+                     optimize=optimize)
         U, Ul = sol.to_device(W0)
         dt0 = dt_h * L / n if dt_h else float(sol.max_dt(U, Ul, cfl)[0])
         steps = int(np.ceil(T / dt0 - 1e-12))
@@ -577,6 +732,18 @@ def run_dmr(args):
     print(json.dumps({"dmr": out, "t": T, "cfl": args.cfl}), flush=True)
 
 
+def ladder_orders(rows, precisions):
+    """Observed orders between consecutive rows of a ladder (mesh ratio from the cell counts)."""
+    for prec in precisions:
+        for a, b in zip(rows[:-1], rows[1:]):
+            if "l1" not in a.get(prec, {}) or "l1" not in b.get(prec, {}):
+                continue
+            r = (b["cells"] / a["cells"]) ** 0.5
+            b[prec]["order_l1"] = float(np.log(a[prec]["l1"] / b[prec]["l1"]) / np.log(r))
+            b[prec]["order_linf"] = float(np.log(a[prec]["linf"] / b[prec]["linf"]) / np.log(r))
+    return rows
+
+
 def run_accuracy(args):
     """Convergence ladders to t = 2 through the CUDA path: FP64 and FP32C, L1 / Linf of rho vs exact."""
     ladders = {name: [int(x) for x in (args.ladder_dw if fam[2] == 2.0 else args.ladder_vortex).split(",")]
@@ -592,16 +759,54 @@ def run_accuracy(args):
                                not args.raw_weights, args.dt_h)
             rows.append(row)
             print(json.dumps({"family": name, **row}), flush=True)
-        for prec in args.precisions.split(","):
-            for a, b in zip(rows[:-1], rows[1:]):
-                if "l1" not in a.get(prec, {}) or "l1" not in b.get(prec, {}):
-                    continue
-                r = (b["cells"] / a["cells"]) ** 0.5
-                b[prec]["order_l1"] = float(np.log(a[prec]["l1"] / b[prec]["l1"]) / np.log(r))
-                b[prec]["order_linf"] = float(np.log(a[prec]["linf"] / b[prec]["linf"]) / np.log(r))
-        out[name] = rows
+        out[name] = ladder_orders(rows, args.precisions.split(","))
     print(json.dumps({"accuracy": out, "t": T, "cfl": args.cfl, "dt_h": args.dt_h, "eps": args.eps,
                       "characteristic": args.characteristic, "optimized_weights": not args.raw_weights}), flush=True)
+
+
+def run_vortex4m_t2(args):
+    """The benchmark workload itself run to t = 2 in FP32C (about 1.6e5 RK3 steps on the 4.0M-cell
+    low-quality mesh): L1 / Linf of rho against the exact translated vortex and the conservation
+    drift.  The FP64 path would take hours at this size; its error comes from the ladder of the
+    same mesh family (--accuracy --families vortex-lowq)."""
+    import torch
+    import synthetic as S
+    from paper_1712_08317_gb300.api import Mesh, Solver
+    T = 2.0
+    mi = S.stretched_vortex_mesh(args.n, seed=0)
+    mesh = Mesh.from_input(mi)
+    W0 = S.cell_average(mi, S.isentropic_vortex, order=4)
+    sol = Solver(mesh, eqn="euler", precision="fp32c", eps=args.eps)
+    U, Ul = sol.to_device(W0)
+    sol.autotune(U, Ul)
+    dt0 = float(sol.max_dt(U, Ul, args.cfl)[0])
+    steps = int(np.ceil(T / dt0 - 1e-12))
+    dt = T / steps
+    c0 = sol.conservation(U, Ul)[0]
+    t0 = time.perf_counter()
+    for k in range(steps):
+        sol.step(U, Ul, dt)
+        if (k + 1) % 20000 == 0:
+            torch.cuda.synchronize()
+            print(json.dumps({"progress": k + 1, "of": steps, "seconds": time.perf_counter() - t0}), flush=True)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    status = "ok"
+    try:
+        sol.check()
+    except Exception as exc:
+        status = str(exc).split(":")[0]
+    W = sol.to_host(U, Ul)
+    ex = S.cell_average(mi, lambda x, y: S.isentropic_vortex(x, y, T), order=4)
+    area = _cell_areas(mi)
+    e = np.abs(W[0] - ex[0])
+    c1 = sol.conservation(U, Ul)[0]
+    print(json.dumps({"vortex4m_t2": {
+        "workload": workload_name(args.n), "cells": mi.n_cells, "precision": "fp32c", "eps": args.eps,
+        "cfl": args.cfl, "t": T, "steps": steps, "dt": dt, "seconds": el, "status": status,
+        "l1_rho": float((e * area).sum() / area.sum()), "l1_int_rho": float((e * area).sum()),
+        "linf_rho": float(e.max()), "conservation_rel_drift": float(np.abs(c1 - c0).max() / np.abs(c0).max())}}),
+        flush=True)
 
 
 def parse_args(argv=None):
@@ -621,7 +826,7 @@ def parse_args(argv=None):
     ap.add_argument("--acc-n", type=int, default=160, help="density-wave mesh of the t = 2 accuracy block (0: skip)")
     ap.add_argument("--ladder-dw", default="20,40,80,160,320")
     ap.add_argument("--ladder-vortex", default="40,80,160")
-    ap.add_argument("--eps", type=float, default=1e-6, help="epsilon of the nonlinear weights (accuracy mode)")
+    ap.add_argument("--eps", type=float, default=1e-3, help="epsilon of the nonlinear weights (accuracy mode)")
     ap.add_argument("--cfl", type=float, default=0.5, help="CFL number of the accuracy runs")
     ap.add_argument("--dt-h", type=float, default=None, help="accuracy mode: fixed dt = dt_h * h (Section 4: 0.3)")
     ap.add_argument("--precisions", default="fp64,fp32c")
@@ -639,6 +844,7 @@ def parse_args(argv=None):
     ap.add_argument("--dmr-diagonal", default="random", choices=["random", "0", "1"],
                     help="diagonal along which the DMR triangle meshes split their quads")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
+    ap.add_argument("--vortex4m-t2", action="store_true", help="the benchmark workload in FP32C to t = 2 vs exact")
     return ap.parse_args(argv)
 
 
@@ -659,6 +865,9 @@ def main():
     if args.dmr:
         run_dmr(args)
         return
+    if args.vortex4m_t2:
+        run_vortex4m_t2(args)
+        return
     assert args.warmup >= 3, "at least 3 warm-up steps"
     import torch
     dist, rank, ws = dist_setup()
@@ -666,10 +875,14 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample()[0]
+        # before the first CUDA call (the pool is spawn-started either way)
+        one = oracle_sample(cores=1)
+        allc = oracle_sample(cores=os.cpu_count() or 1)
+        cpu = dict(allc)
+        cpu["single_core"] = {"value": one["value"], "sample": one["sample"]}
 
     import synthetic as S
-    from paper_1712_08317_gb300.api import Mesh, Solver
+    from paper_1712_08317_gb300.api import Mesh, Solver, params_struct
     t_setup = time.perf_counter()
     mi = S.stretched_vortex_mesh(args.n, seed=rank)
     mesh = Mesh.from_input(mi)
@@ -683,6 +896,7 @@ def main():
     if not args.no_autotune:
         sol.autotune(U, Ul)
     stream = torch.cuda.current_stream()
+    peaks = measure_peaks()  # the pipe peaks of this GPU, before the timed region
     for _ in range(args.warmup):
         sol.step(U, Ul, dt)
     torch.cuda.synchronize()
@@ -743,11 +957,11 @@ def main():
     kbytes = k1_bytes(nQ, nT, 4, 4, True)
     achieved = kbytes / (k_ms / 1e3) / 1e9
     kops = k1_ops(nQ, nT)
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = (clk.get("sm_max_mhz") if isinstance(clk, dict) else None) or 2070.0
-    alu_peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    alu_peak = peaks["fp32_fma"]
     alu_achieved = kops / (k_ms / 1e3) / 1e12
-    traffic = (nQ * K1_TRAFFIC_PER_CELL["quad"] + nT * K1_TRAFFIC_PER_CELL["tri"]) if K1_TRAFFIC_PER_CELL else None
+    traffic = k1_traffic(nQ, nT)
+    sbytes = step_bytes(nQ, nT)
+    step_achieved = sbytes * 3 * args.steps / (ms / 1e3) / 1e9
 
     # end to end through the public API with host state: H2D copy, step, D2H copy every step
     hostU = torch.empty(U.shape, dtype=U.dtype, pin_memory=True)
@@ -798,25 +1012,20 @@ def main():
     fp64_ms = max_over_ranks(dist, f0.elapsed_time(f1), dev)
     fp64_value = whole_job_rate(ws, N, 3 * fp64_steps, fp64_ms)
     sol64.check()
+    # the FP64 reconstruction pass alone, against the measured FP64 FMA peak
+    sol64.run_pass(1, V)
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(3):
+        sol64.run_pass(1, V)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    k64_ms = d0.elapsed_time(d1) / 3
+    k64_ops = k1_ops_fp64(nQ, nT)
 
-    # accuracy at t = (steps done) dt: FP32C vs FP64 vs the exact translated vortex
-    acc = None
-    if rank == 0:
-        t_fp32 = steps_done * dt
-        # bring FP64 to the same step count
-        for _ in range(steps_done - 3 - fp64_steps):
-            sol64.step(V, None, dt)
-        torch.cuda.synchronize()
-        W32 = sol.to_host(U, Ul)
-        W64 = sol64.to_host(V)
-        ex = S.cell_average(mi, lambda x, y: S.isentropic_vortex(x, y, t_fp32), order=4)
-        area = _cell_areas(mi)
-
-        def l1(d):
-            return float((np.abs(d[0]) * area).sum() / area.sum())
-        acc = {"t": t_fp32, "steps": steps_done, "dt": dt, "l1_rho_fp32c_vs_exact": l1(W32 - ex),
-               "l1_rho_fp64_vs_exact": l1(W64 - ex), "l1_rho_fp32c_vs_fp64": l1(W32 - W64),
-               "conservation_rel_drift_fp32c": float(np.abs(c_end - c_start).max() / np.abs(c_start).max())}
+    conservation = {"rel_drift_fp32c": float(np.abs(c_end - c_start).max() / np.abs(c_start).max()),
+                    "steps": args.warmup + args.steps}
 
     # characteristic-variable reconstruction (Section 4) on the same mesh, FP32C
     char = None
@@ -854,17 +1063,23 @@ def main():
                 "reconstruction": "characteristic variables (Roe-averaged normal Jacobian per face)",
                 "roofline": {"kernel": "k_reconstruct_char_tma (quad + triangle launches of one pass)",
                              "bound": "alu", "achieved": char_ops / (char_k1 / 1e3) / 1e12, "peak": alu_peak,
-                             "unit": "Top/s (FP32 lane ops, FMA = 1)",
+                             "unit": "Top/s (FP32 ops, FMA = 1)",
                              "frac": char_ops / (char_k1 / 1e3) / 1e12 / alu_peak,
                              "algorithmic_ops_per_launch": char_ops, "ms_per_launch": char_k1}}
         del solc, Uc, Ulc
         torch.cuda.empty_cache()
 
-    # accuracy to t = 2 on the density-wave mesh of 51,200 split triangles (FP64 vs FP32C vs exact)
+    # accuracy to t = 2 against the exact solutions, FP64 and FP32C through the CUDA path: config 1
+    # (scalar, 40 x 40 perturbed quads), the density-wave ladder on split triangles up to n = acc_n
+    # (51,200 triangles at 160) and the ladder of the benchmark's own low-quality mesh family
     acc_t2 = None
     if rank == 0 and args.acc_n > 0:
-        acc_t2 = {"family": "densitywave-tri", "t": 2.0, "cfl": 0.5,
-                  **ladder_point("densitywave-tri", args.acc_n, ["fp64", "fp32c"])}
+        precs = ["fp64", "fp32c"]
+        acc_t2 = {"t": 2.0, "cfl": 0.5, "eps": float(params_struct().eps),
+                  "config1_scalar": ladder_point("config1-scalar", 40, precs),
+                  "densitywave_tri": ladder_orders([ladder_point("densitywave-tri", n, precs)
+                                                    for n in (20, 40, 80, args.acc_n)], precs),
+                  "vortex_lowq": ladder_orders([ladder_point("vortex-lowq", n, precs) for n in (40, 80, 160)], precs)}
 
     # k_fill of dt, the three stages, k_advance_time
     launches_per_step = 2 + 3 * ((1 if nQ else 0) + (1 if nT else 0) + 1 + (1 if nQ else 0) + (1 if nT else 0))
@@ -892,20 +1107,29 @@ def main():
             # the reconstruction is bound by FP32 arithmetic (FMA pipe and issue), not by HBM: see
             # profiles/k_reconstruct_tma_n700_fp32c.md; the HBM view the design target names follows
             "roofline": {"kernel": "k_reconstruct_tma (quad + triangle launches of one pass)", "bound": "alu",
-                         "achieved": alu_achieved, "peak": alu_peak, "unit": "Top/s (FP32 lane ops, FMA = 1)",
+                         "achieved": alu_achieved, "peak": alu_peak, "unit": "Top/s (FP32 ops, FMA = 1)",
                          "frac": alu_achieved / alu_peak,
-                         "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz",
+                         "peak_source": "measured FP32 FMA throughput of this GPU (weno_probe_peak)",
                          "traffic": traffic, "algorithmic_ops_per_launch": kops, "ms_per_launch": k_ms},
+            "peaks_measured": {"unit": "Top/s (FMA = 1)", **peaks},
+            "roofline_step_hbm": {"bound": "hbm", "achieved": step_achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": step_achieved / peak, "algorithmic_bytes_per_stage": sbytes,
+                                  "note": "whole RK stage (3 kernels), minimum-traffic model, over the timed steps"},
             "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
                              "algorithmic_bytes_per_launch": kbytes,
                              "traffic_frac": (traffic / (k_ms / 1e3) / 1e9 / peak) if traffic else None},
             "kernel_ms": {"reconstruct": k_ms, "face": face_ms, "gather": gather_ms},
             "fp64": {"value": fp64_value, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64_ms / fp64_steps,
-                     "fp32c_over_fp64": value / fp64_value},
+                     "fp32c_over_fp64": value / fp64_value,
+                     "roofline": {"kernel": "k_reconstruct<double> (quad + triangle launches of one pass)",
+                                  "bound": "alu", "achieved": k64_ops / (k64_ms / 1e3) / 1e12,
+                                  "peak": peaks["dfma"], "unit": "Top/s (FP64 ops, FMA or division = 1)",
+                                  "frac": k64_ops / (k64_ms / 1e3) / 1e12 / peaks["dfma"],
+                                  "algorithmic_ops_per_launch": k64_ops, "ms_per_launch": k64_ms}},
             "batched": batched,
             "characteristic": char,
-            "accuracy": acc,
+            "conservation": conservation,
             "accuracy_t2": acc_t2,
             "cpu_baseline": cpu,
         }

@@ -111,7 +111,7 @@ class Mesh:
             self._h = None
 
 
-def params_struct(eqn="euler", precision="fp64", gas_gamma=1.4, adv=(1.0, 1.0), eps=1e-6, theta=3.0,
+def params_struct(eqn="euler", precision="fp64", gas_gamma=1.4, adv=(1.0, 1.0), eps=1e-3, theta=3.0,
                   rcond=1e-12, optimize=True, linear=False, n_threads=0, characteristic=False, inflow_a=None,
                   inflow_b=None, inflow_line=(1.0, 0.0, 0.0, 0.0)):
     p = capi.weno_params()

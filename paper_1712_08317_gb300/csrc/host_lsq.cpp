@@ -309,7 +309,11 @@ void cell_tables(const Mesh& m, const LsqParams& p, int64_t c, GroupTables& T, i
       eta[0] = 1.0 - sum;
       minnorm_cod(B, R, M, eta, 1, p.rcond, gam);
     }
+    // sum_j gamma_j = 1 (Section 3.1) holds for the exact solution; impose it on the computed one
+    double gsum = 0.0;
+    for (int j = 0; j < M; ++j) gsum += gam[j];
     for (int j = 0; j < M; ++j) {
+      gam[j] /= gsum;
       T.gam[(g * M + j) * N + q] = gam[j];
       mopt = std::max(mopt, std::fabs(gam[j]));
     }

@@ -6,7 +6,8 @@
 //   kind 0  FP32 fused multiply-add, scalar   (fma.rn.f32)
 //   kind 1  FP32 fused multiply-add, paired   (__ffma2_rn: two FMAs per instruction)
 //   kind 2  FP64 fused multiply-add           (fma.rn.f64)
-//   kind 3  FP32 approximate reciprocal        (rcp.approx.ftz.f32, the MUFU pipe)
+//   kind 3  FP32 approximate reciprocal        (rcp.approx.ftz.f32, the MUFU pipe; each also
+//           takes one FP32 add on the FMA pipe, whose rate is far higher)
 // An FMA counts as one operation.  The chains' results are stored, so nothing
 // is dead code.
 #include <cuda_runtime.h>
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_probe_dfma(double b, double c, int
 
 __device__ __forceinline__ float probe_rcp(float x) {
   float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_probe_rcp(float b, float c, int it
   for (int k = 0; k < kChains; ++k) a[k] = b + c * (float)(threadIdx.x + k + 1);
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) a[k] = probe_rcp(a[k]);
+    for (int k = 0; k < kChains; ++k) a[k] = probe_rcp(a[k] + c);  // not an involution: nothing folds
   }
   float s = 0.f;
 #pragma unroll

@@ -99,7 +99,7 @@ struct weno_solver_s {
   int64_t q_pitch = 0, t_pitch = 0;  // row pitch (cells) of the packed FP32C tables
   bool tma = false;                   // Euler FP32C: reconstruction with TMA-staged tables
   CUtensorMap q_map_gpm{}, q_map_dgs{}, t_map_gpm{}, t_map_dgs{}, t_map_g1{};
-  CUtensorMap q_map_gop{}, t_map_gop{};  // gradient operators (characteristic reconstruction)
+  CUtensorMap q_map_gop{}, t_map_gop{};  // gradient operators
   int* err = nullptr;                 // set by a kernel whose bounded wait timed out
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
   void *area = nullptr, *inv_area = nullptr, *inv_area_lo = nullptr;
@@ -201,12 +201,12 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
       using TT = weno::dev::TmaTile<9, 6>;
       if (s.nQ && (which & 1))
         weno::dev::k_reconstruct_tma<12, 8, WALLS><<<tma_grid(s.k1q, s.nQ), TQ::THREADS, TQ::SMEM, st>>>(
-            s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
-            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
+            s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
+            (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       if (s.nT && (which & 2))
         weno::dev::k_reconstruct_tma<9, 6, WALLS><<<tma_grid(s.k1t, s.nT), TT::THREADS, TT::SMEM, st>>>(
-            s.t_map_gpm, s.t_map_dgs, s.t_map_g1, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
-            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
+            s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
+            8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       return;
     }
   }
@@ -488,12 +488,12 @@ int setup_tma(S& s) {
                           TQ::SMEM));
   CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           TT::SMEM));
+  // D_j^+ rows: M float4 rows
+  if (s.nQ && (r = make_map_2d(enc, &s.q_map_gop, s.q_gop, 4 * s.q_pitch, 12, 16 * s.q_pitch, 4 * kTile, 12)))
+    return r;
+  if (s.nT && (r = make_map_2d(enc, &s.t_map_gop, s.t_gop, 4 * s.t_pitch, 9, 16 * s.t_pitch, 4 * kTile, 9)))
+    return r;
   if (s.prm.characteristic) {
-    // D_j^+ rows: M float4 rows
-    if (s.nQ && (r = make_map_2d(enc, &s.q_map_gop, s.q_gop, 4 * s.q_pitch, 12, 16 * s.q_pitch, 4 * kTile, 12)))
-      return r;
-    if (s.nT && (r = make_map_2d(enc, &s.t_map_gop, s.t_gop, 4 * s.t_pitch, 9, 16 * s.t_pitch, 4 * kTile, 9)))
-      return r;
     for (auto fn : {weno::dev::k_reconstruct_char_tma<12, 8, false>, weno::dev::k_reconstruct_char_tma<12, 8, true>})
       CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::CharTile<12, 8>::SMEM));
     for (auto fn : {weno::dev::k_reconstruct_char_tma<9, 6, false>, weno::dev::k_reconstruct_char_tma<9, 6, true>})
@@ -520,7 +520,7 @@ void weno_params_default(weno_params* p) {
   p->gas_gamma = 1.4;
   p->adv[0] = 1.0;
   p->adv[1] = 1.0;
-  p->eps = 1e-6;
+  p->eps = 1e-3;
   p->theta = 3.0;
   p->rcond = 1e-12;
   p->optimize = 1;

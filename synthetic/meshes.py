@@ -239,14 +239,16 @@ def stretched_vortex_mesh(n: int, frac=0.3, delta=0.4, seed=0, L=10.0):
                      f"vortex-lowq-n{n}", {"n": n, "split": frac, "delta": delta})
 
 
-def periodic_mesh(n: int, L: float, kind: str = "quad", delta: float = 0.1, seed: int = 0) -> MeshInput:
+def periodic_mesh(n: int, L: float, kind: str = "quad", delta: float = 0.1, seed: int = 0,
+                  diagonal: int | None = None) -> MeshInput:
     """Periodic [0, L]^2 grid of n x n quads whose interior nodes are displaced by up to delta of the
     spacing (delta = 0: regular), kept as quads ("quad"), all split into triangles ("tri") or 30 %
-    split ("mixed") along random diagonals: the regular and irregular meshes of the accuracy tests."""
+    split ("mixed") along random diagonals or the one `diagonal` names (see split_quads): the
+    regular and irregular meshes of the accuracy tests."""
     frac = {"quad": 0.0, "tri": 1.0, "mixed": 0.3}[kind]
     pos, quads = perturbed_quads(n, (0.0, 0.0), (L, L), delta, seed)
     return _assemble(pos, quads, frac, seed, "periodic", (0.0, 0.0), (L, L), f"periodic-{kind}-n{n}-d{delta}",
-                     {"n": n, "split": frac, "delta": delta})
+                     {"n": n, "split": frac, "delta": delta, "diagonal": diagonal}, diagonal)
 
 
 def mesh_for_config(config: int, n: int | None = None, seed: int = 0, kind: str | None = None) -> MeshInput:

@@ -70,6 +70,19 @@ def _rel(a, b):
     return float((np.abs(a - b) / scale).max())
 
 
+def _flux_scale(osol, W):
+    """Per cell and variable, the magnitude of the terms its residual sums: sum_f |F_f| / |Omega_i|.
+    A residual is a cancelling sum of face fluxes, so its rounding (and any faithful difference
+    between two implementations) is relative to this, not to |R_i|, which can be ~0 while the
+    fluxes are O(1)."""
+    F = osol.face_fluxes(W)
+    S_ = np.zeros_like(W)
+    np.add.at(S_, (slice(None), osol.fL), np.abs(F))
+    inner = ~osol.boundary
+    np.add.at(S_, (slice(None), osol.fR[inner]), np.abs(F[:, inner]))
+    return S_ / osol.mesh.area[None, :]
+
+
 def _rel_cell(a, b):
     return float((np.abs(a - b).max(axis=0) / np.abs(b).max(axis=0)).max())
 
@@ -83,6 +96,12 @@ def test_fp64_residual_matches_oracle(name):
     R = sol.to_host(sol.residual(U))
     sol.check()
     assert _rel(R, ref) < TOL_FP64
+    # cell by cell: against the cell's own flux magnitudes, and against |R_i| where the residual is
+    # not a near-total cancellation (|R_i| above 1% of the largest)
+    d = np.abs(R - ref)
+    assert float((d / _flux_scale(osol, W)).max()) < TOL_FP64
+    big = np.abs(ref) > 1e-2 * np.abs(ref).max(axis=1, keepdims=True)
+    assert float((d[big] / np.abs(ref[big])).max()) < 10 * TOL_FP64
 
 
 @pytest.mark.parametrize("name", list(CASES))

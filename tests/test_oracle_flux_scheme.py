@@ -197,22 +197,60 @@ def test_third_order_convergence_of_the_linear_scheme():
     assert orders[-1] > 2.7, (errs, orders)
 
 
-def test_nonlinear_scheme_converges():
-    """Nonlinear weights (eps = 1e-6): errors fall along the ladder.
-
-    These coarse meshes are pre-asymptotic for the nonlinear weights (beta >> eps
-    near critical points), so only the decrease is pinned here; the rate on
-    finer meshes is checked through the CUDA path, itself pinned to this oracle.
-    """
+def test_nonlinear_scheme_is_third_order_on_config_1():
+    """Scalar advection u_t + u_x + u_y = 0 on periodic [0,2]^2 perturbed quads (delta = 0.1), t = 2,
+    CFL 0.5, the full nonlinear scheme of Section 3.4 (eps = 1e-3) against the exact translated wave:
+    L1 and L-infinity orders of at least 2.7 between n = 40 and 80 (the method is third order; the
+    error falls faster while the nonlinear weights approach the linear ones, as in the paper's
+    Tables 3-6).  n = 40 is the 1,600-cell configuration of the benchmark description."""
     errs = []
-    for n in (10, 20, 40):
+    for n in (20, 40, 80):
         mi = S.mesh_for_config(1, n=n, seed=0)
         mesh = OracleMesh.from_input(mi)
         sol = OracleSolver(mesh, Params(eqn="scalar"))
         W = S.cell_average(mi, S.scalar_wave)
-        W, _, _ = sol.run(W, 0.5, 0.5)
-        ex = S.cell_average(mi, lambda x, y: S.scalar_wave(x, y, 0.5))
-        errs.append(float((np.abs(W - ex)[0] * mesh.area).sum() / mesh.area.sum()))
-    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    assert errs[0] > errs[1] > errs[2]
-    assert errs[0] / errs[2] > 4.0, (errs, orders)
+        W, _, _ = sol.run(W, 2.0, 0.5)
+        e = np.abs(W - S.cell_average(mi, lambda x, y: S.scalar_wave(x, y, 2.0)))[0]
+        errs.append(((e * mesh.area).sum() / mesh.area.sum(), e.max()))
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])
+    assert (orders[-1] >= 2.7).all(), (errs, orders)
+    assert errs[1, 0] < 1e-2 and errs[2, 0] < 1e-3          # config 1 (n = 40): L1 5.2e-3, Linf 1.2e-2
+
+
+def _density_wave_errors(n, eps):
+    """The paper's first accuracy test on a regular n x n quad mesh of [0,2]^2: rho errors at t = 2
+    with dt = 0.3 h, as (sum |Omega| |e|, max |e|)."""
+    nodes, quads, _, _ = S.quad_grid(n, (0.0, 0.0), (2.0, 2.0))
+    mi = S.MeshInput(nodes, np.arange(0, 4 * n * n + 1, 4), quads.ravel(), "periodic", (0, 0), (2, 2))
+    mesh = OracleMesh.from_input(mi)
+    sol = OracleSolver(mesh, Params(eps=eps))
+    W = S.cell_average(mi, S.density_wave)
+    h = 2.0 / n
+    steps = int(np.ceil(2.0 / (0.3 * h) - 1e-12))
+    dt = 2.0 / steps
+    t = 0.0
+    for _ in range(steps):
+        W = sol.rk3_step(W, dt, t=t)
+        t += dt
+    e = np.abs(W[0] - S.cell_average(mi, lambda x, y: S.density_wave(x, y, 2.0))[0])
+    return float((e * mesh.area).sum()), float(e.max())
+
+
+def test_density_wave_on_regular_quads_reproduces_table_3():
+    """Section 4, first accuracy test, regular quadrilateral meshes (Table 3): with the nonlinear
+    weights of Section 3.4 at eps = 1e-3 the oracle gives the paper's printed L1 and L-infinity errors
+    at h = 1/8 and 1/16 to within 5 % and their orders to within 0.1 (the CUDA path is checked against
+    all four rows).  The regular mesh is the one mesh of the paper that can be rebuilt exactly, so
+    this pins the whole scheme (stencils, least squares, optimised and split linear weights, new
+    indicator, HLLC, SSP-RK3) to the paper's digits; eps = 1e-6 misses them by a factor 2.4 already
+    at h = 1/16 (the reading of eps)."""
+    ref = np.loadtxt(__file__.replace("test_oracle_flux_scheme.py", "golden/table3_density_wave_quad_regular.txt"))
+    got = [_density_wave_errors(int(round(2.0 / h)), 1e-3) for h in ref[:2, 0]]
+    for (l1, li), row in zip(got, ref[:2]):
+        assert abs(l1 / row[1] - 1.0) < 0.05, (l1, row[1])
+        assert abs(li / row[3] - 1.0) < 0.05, (li, row[3])
+    assert abs(np.log2(got[0][0] / got[1][0]) - ref[1, 2]) < 0.1
+    assert abs(np.log2(got[0][1] / got[1][1]) - ref[1, 4]) < 0.1
+    l1_small_eps, _ = _density_wave_errors(32, 1e-6)
+    assert l1_small_eps > 2.0 * ref[1, 1]

@@ -70,6 +70,7 @@ def test_candidates_reproduce_linear_functions(outflow_case):
 def test_linear_weights_sum_to_one_and_solve_the_system(outflow_case):
     _, _, groups = outflow_case
     for t in groups:
+        assert np.abs(t.gamma.sum(-1) - 1.0).max() < 1e-14           # imposed on the run-time weights
         for gam, eta in ((t.gamma_raw, t.eta_raw), (t.gamma, t.eta)):
             assert np.abs(gam.sum(-1) - 1.0).max() < 1e-10          # Section 3.1: sum gamma_j = 1
             res = np.einsum("ngrm,ngm->ngr", t.B, gam) - eta

@@ -67,7 +67,7 @@ def test_splitting_is_identity_for_positive_weights():
     P = W0[:, None, None] + np.einsum("nma,nga->ngm", g, t.dG)
     beta = (t.area[:, None] * (g ** 2).sum(-1))[:, None, :]
     q = pos * beta
-    a = pos / (beta * (1 + q + q * q) + 1e-6) ** 2
+    a = pos / (beta * (1 + q + q * q) + Params().eps) ** 2
     ref = (a * P).sum(-1) / a.sum(-1)
     assert np.abs(R - ref).max() < 1e-12
 
