@@ -33,7 +33,8 @@ FALLBACK_HBM_GBS = 6800.0
 # k_reconstruct_tma on the 637k-cell mesh of the benchmark family (n = 700), divided by its cells of
 # each type.  They describe the kernel source they were captured on (SHA-256 of csrc/kernels.cuh);
 # for any other source the bench line reports traffic null.
-K1_TRAFFIC = {"kernels_cuh_sha256": None, "quad": None, "tri": None}
+K1_TRAFFIC = {"kernels_cuh_sha256": "d679aebe3ecd0b9c3e312a1935736c67ae9f26fb327f12a6b8a01fbed75d053d",
+              "quad": 1306.7, "tri": 851.2}
 WORKLOAD_N = 1754
 
 
@@ -805,7 +806,10 @@ def run_vortex4m_t2(args):
         "workload": workload_name(args.n), "cells": mi.n_cells, "precision": "fp32c", "eps": args.eps,
         "cfl": args.cfl, "t": T, "steps": steps, "dt": dt, "seconds": el, "status": status,
         "l1_rho": float((e * area).sum() / area.sum()), "l1_int_rho": float((e * area).sum()),
-        "linf_rho": float(e.max()), "conservation_rel_drift": float(np.abs(c1 - c0).max() / np.abs(c0).max())}}),
+        "linf_rho": float(e.max()), "conservation_rel_drift": float(np.abs(c1 - c0).max() / np.abs(c0).max()),
+        # isolated instabilities at sliver cells of this mesh: how many, and L1 over the other cells
+        "cells_err_gt": {f"{th:g}": int((e > th).sum()) for th in (1e-3, 1e-2, 1e-1)},
+        "l1_rho_without_cells_err_gt_1e-2": float((e * area)[e <= 1e-2].sum() / area[e <= 1e-2].sum())}}),
         flush=True)
 
 
@@ -1104,8 +1108,8 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "steps": e2e_steps},
-            # the reconstruction is bound by FP32 arithmetic (FMA pipe and issue), not by HBM: see
-            # profiles/k_reconstruct_tma_n700_fp32c.md; the HBM view the design target names follows
+            # the reconstruction is bound by its arithmetic (the FMA pipe and the reciprocals' MUFU pipe,
+            # each about half of its time), not by HBM; the HBM views follow
             "roofline": {"kernel": "k_reconstruct_tma (quad + triangle launches of one pass)", "bound": "alu",
                          "achieved": alu_achieved, "peak": alu_peak, "unit": "Top/s (FP32 ops, FMA = 1)",
                          "frac": alu_achieved / alu_peak,

@@ -93,7 +93,9 @@ typedef struct {
   double adv[2];      /* advection velocity (scalar)                                       */
   double eps;         /* epsilon of the nonlinear weights, Section 3.4, whose value the paper
                          does not state; default 1e-3, with which the scheme reproduces the
-                         paper's Table 3 (density wave on regular quads) to about 1 %        */
+                         paper's Table 3 (density wave on regular quads) to about 1 %.  FP32C
+                         solvers need eps >= 1e-15 (WENO_EINVAL otherwise), which keeps the
+                         FP32 weights alpha <= 1 / eps^2 in range                           */
   double theta;       /* splitting parameter of Section 3.4 (3); must exceed 1, which keeps
                          sigma- > 0 (weno_solver_create returns WENO_EINVAL otherwise)      */
   double rcond;       /* relative singular-value cut of the minimum-norm least squares that

@@ -266,6 +266,24 @@ __device__ __noinline__ float nonlinear_increment_fp64(const float* __restrict__
   return (float)((double)sp * (Bp / Ap) - (double)sm * (Bm / Am));
 }
 
+constexpr float kAlphaMin = 1e-30f;  // smallest sum of alpha the FP32 weights accept (see gauss_increment)
+
+// Nonlinear weights of one candidate pair (or, scalar, of one candidate) at one Gauss point:
+// alpha+- = gamma+- / (beta~+- + eps)^2 with beta~+- = beta (1 + q + q^2), q = gamma+- beta.
+__device__ __forceinline__ void pair_alpha(float2 gp, float2 gn, float2 b, float2 be, float2& ap, float2& an) {
+  const float2 qp = __fmul2_rn(gp, b), qn = __fmul2_rn(gn, b);
+  const float2 dp = __ffma2_rn(b, __ffma2_rn(qp, qp, qp), be);   // beta~+ + eps
+  const float2 dn = __ffma2_rn(b, __ffma2_rn(qn, qn, qn), be);   // beta~- + eps
+  ap = __fmul2_rn(gp, rcp2(__fmul2_rn(dp, dp)));
+  an = __fmul2_rn(gn, rcp2(__fmul2_rn(dn, dn)));
+}
+__device__ __forceinline__ void one_alpha(float gp, float gn, float b, float be, float& ap, float& an) {
+  const float qp = gp * b, qn = gn * b;
+  const float dp = fmaf(b, fmaf(qp, qp, qp), be), dn = fmaf(b, fmaf(qn, qn, qn), be);
+  ap = gp * rcp_approx(dp * dp);
+  an = gn * rcp_approx(dn * dn);
+}
+
 // Increment R(x_G) - W0 of one Gauss point (Section 3.4, FP32) from the
 // candidate pairs and the split linear weights gamma+ (gpos), gamma- (gneg)
 // with their sums sigma+- (sp, sm), which depend on geometry only and are
@@ -274,10 +292,13 @@ __device__ __noinline__ float nonlinear_increment_fp64(const float* __restrict__
 //   delta+-_j = alpha+-_j / sum alpha+-, alpha+-_j = gamma+-_j / (beta~+-_j + eps)^2,
 //   beta~+-_j = beta_j (1 + q + q^2), q = gamma+-_j beta_j.
 // The linear scheme is R - W0 = sum gamma_j p_j = sigma+ sum gamma+ p - sigma- sum gamma- p.
-template <int P>
-__device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const float2* gpos, const float2* gneg,
-                                                 float dx, float dy, float sp, float sm, int linear, bool& redo) {
-  redo = false;
+// With M odd the last candidate (the .x lane of the last pair) is evaluated in scalar arithmetic.
+template <int M>
+__device__ __forceinline__ float gauss_increment(const CandPairs<(M + 1) / 2>& c, const float2* gpos,
+                                                 const float2* gneg, float dx, float dy, float sp, float sm,
+                                                 int linear, float& amin) {
+  constexpr int P = (M + 1) / 2, FULL = M / 2;
+  amin = 1.0f;
   const float2 dx2 = f2(dx, dx), dy2 = f2(dy, dy);
   if (linear) {
     float2 ap = f2(0.f, 0.f), an = f2(0.f, 0.f);
@@ -292,13 +313,10 @@ __device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const fl
   // sums of alpha+- and alpha+- p: pair 0 initialises them, later pairs add
   float2 Ap, Bp, Am, Bm;
 #pragma unroll
-  for (int k = 0; k < P; ++k) {
+  for (int k = 0; k < FULL; ++k) {
     const float2 p = __ffma2_rn(c.gx[k], dx2, __fmul2_rn(c.gy[k], dy2));  // P^1_j(x_G) - W0
-    const float2 qp = __fmul2_rn(gpos[k], c.b[k]), qn = __fmul2_rn(gneg[k], c.b[k]);
-    const float2 bp = __ffma2_rn(c.b[k], __ffma2_rn(qp, qp, qp), c.be[k]);
-    const float2 bn = __ffma2_rn(c.b[k], __ffma2_rn(qn, qn, qn), c.be[k]);
-    const float2 ap = __fmul2_rn(gpos[k], rcp2(__fmul2_rn(bp, bp)));
-    const float2 an = __fmul2_rn(gneg[k], rcp2(__fmul2_rn(bn, bn)));
+    float2 ap, an;
+    pair_alpha(gpos[k], gneg[k], c.b[k], c.be[k], ap, an);
     if (k == 0) {
       Ap = ap; Bp = __fmul2_rn(ap, p);
       Am = an; Bm = __fmul2_rn(an, p);
@@ -307,14 +325,19 @@ __device__ __forceinline__ float gauss_increment(const CandPairs<P>& c, const fl
       Am = __fadd2_rn(Am, an); Bm = __ffma2_rn(an, p, Bm);
     }
   }
-  const float As = Ap.x + Ap.y, Bs = Bp.x + Bp.y, Ams = Am.x + Am.y, Bms = Bm.x + Bm.y;
-  // The FP32 weights are exact up to rounding while each group's sum of alpha stays in
-  // [kAlphaLo, kAlphaHi]: then (beta~ + eps)^2 of every candidate that matters is far from
-  // overflow and its reciprocal far from the flush-to-zero range.  Outside it (indicators of
-  // order 1e6 and more at strong jumps, or a tiny eps) the caller evaluates the Gauss point
-  // again with gauss_increment_fp64.
-  constexpr float kAlphaLo = 1e-30f, kAlphaHi = 1e30f;
-  redo = !(As >= kAlphaLo && As <= kAlphaHi && Ams >= kAlphaLo && Ams <= kAlphaHi);
+  float As = Ap.x + Ap.y, Bs = Bp.x + Bp.y, Ams = Am.x + Am.y, Bms = Bm.x + Bm.y;
+  if constexpr (M % 2 == 1) {
+    const float p = fmaf(c.gx[P - 1].x, dx, c.gy[P - 1].x * dy);
+    float ap, an;
+    one_alpha(gpos[P - 1].x, gneg[P - 1].x, c.b[P - 1].x, c.be[P - 1].x, ap, an);
+    As += ap; Bs = fmaf(ap, p, Bs);
+    Ams += an; Bms = fmaf(an, p, Bms);
+  }
+  // The smaller sum of alpha of the two groups: the caller redoes the Gauss point in FP64 when it
+  // falls below kAlphaMin (indicators of order 1e6 and more, whose (beta~ + eps)^2 overflows FP32
+  // or whose reciprocal flushes).  Above it every candidate that matters is far from both limits;
+  // the sums never exceed 1 / eps^2 <= 1e30, since eps >= 1e-15 for FP32 weights.
+  amin = fminf(As, Ams);
   return sp * Bs * rcp_approx(As) - sm * Bms * rcp_approx(Ams);
 }
 
@@ -405,43 +428,39 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
         gn[P - 1] = f2(e.y, 0.f);
       }
     };
-    uint32_t redo = 0u;  // Gauss points whose weights left the FP32 range
+    float amin = 1.0f;  // smallest sum of alpha over the Gauss points
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
       float4 d;
       float2 gp[P], gn[P];
       tables(g, d, gp, gn);
-      bool r;
-      const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, r);
-      redo |= (uint32_t)r << g;
+      float am;
+      const float incr = gauss_increment<M>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, am);
+      amin = fminf(amin, am);
       out[(int64_t)g * NV] = w0 + (l0 + incr);
     }
+    if (!(amin >= kAlphaMin)) {  // weights outside the FP32 range (rare): every point again in FP64
 #pragma unroll 1
-    for (int g = 0; redo != 0u; ++g, redo >>= 1) {
-      if (!(redo & 1u)) continue;
-      float4 d;
-      float2 gp[P], gn[P];
-      tables(g, d, gp, gn);
-      out[(int64_t)g * NV] = w0 + (l0 + gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps));
+      for (int g = 0; g < G; ++g) {
+        float4 d;
+        float2 gp[P], gn[P];
+        tables(g, d, gp, gn);
+        out[(int64_t)g * NV] = w0 + (l0 + gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps));
+      }
     }
   }
 }
 
-// ---------------------------------------------------------------- K1 with asynchronously staged inputs
+// ---------------------------------------------------------------- K1 with TMA-staged tables
 // Euler FP32C, one block per tile or persistent: a tile is TILE consecutive cells of one type,
-// one (cell, variable) per thread.  Every input of a tile reaches shared memory asynchronously
-// while the block computes the tile before it:
-//   * the stencil states (hi and lo of the cell and its M stencil cells) by 16-byte cp.async
-//     copies, issued by all threads for tile i+1 right after tile i's gradient phase (the
-//     stencil entries of tile i+1 are prefetched into registers at the start of tile i);
-//   * the candidate gradient operators D_j^+ by a 2D TMA copy (cp.async.bulk.tensor) issued
-//     at the same point, completing on mbarrier 1;
-//   * the split linear weights, Gauss offsets and sigma+- by TMA copies issued when tile i's
-//     Gauss-point loop has finished with them, completing on mbarrier 0 (the next tile's
-//     gradient phase and the other resident blocks hide their latency).
-// So no warp waits on a global load inside a tile.  The gathered states are stored with a
-// row of 4 (M + 1) words per cell rounded to an odd multiple of 4, so the 8 cells of a warp
-// read distinct banks.  Every mbarrier wait is bounded: on timeout the block records
+// one (cell, variable) per thread.  One elected thread loads the tile's split
+// linear weights and Gauss offsets into shared memory with 2D TMA copies
+// (cp.async.bulk.tensor) completing on an mbarrier; the stencil gathers of the
+// tile are issued before the wait.  With one buffer (default) the next tile's
+// copy starts when the block has finished reading the current one and the
+// other resident block hides its latency, which leaves more of the unified
+// L1 to the gathers than two buffers would; WENO_K1_STAGES=2 prefetches the
+// next tile instead.  Every wait is bounded: on timeout the block records
 // *err = 1, drains its copies (bounded) and exits.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -489,14 +508,9 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 #endif
 static_assert(WENO_K1_TILE == 8 || WENO_K1_TILE == 16 || WENO_K1_TILE == 32 || WENO_K1_TILE == 64, "tile of 8, 16, 32 or 64 cells");
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+#ifndef WENO_K1_STAGES
+#define WENO_K1_STAGES 1  // shared-memory table buffers per block (2: prefetch the next tile while computing)
+#endif
 
 template <int M, int G>
 struct TmaTile {
@@ -506,77 +520,24 @@ struct TmaTile {
   static constexpr int GPM = G * 2 * M4 * TILE * 16;          // gamma+ rows then gamma- rows
   static constexpr int DGS = G * TILE * 16;                    // (x_G - c0, sigma+, sigma-)
   static constexpr int G1 = (M % 4) ? G * TILE * 8 : 0;        // (gamma+_8, gamma-_8) of triangles
-  static constexpr int WTS = GPM + DGS + G1;                   // TMA group on mbarrier 0
-  static constexpr int GOP = M * TILE * 16;                    // D_j^+ rows: TMA group on mbarrier 1
-  static constexpr int SW = 4 * ((M + 1) | 1);                 // words per cell row of gathered states
-  static constexpr int STATE = TILE * SW * 4;                  // bytes of the hi rows (and of the lo rows)
-  static constexpr int RAW = M * TILE * 4;                     // stencil entries of one tile
-  static constexpr int PER_THREAD = (M * TILE + THREADS - 1) / THREADS;  // stencil entries a thread copies
-  static constexpr int OFF_GOP = WTS, OFF_HI = OFF_GOP + GOP, OFF_LO = OFF_HI + STATE, OFF_RAW = OFF_LO + STATE;
-  static constexpr int OFF_BAR = OFF_RAW + 2 * ((RAW + 15) / 16 * 16);  // two tiles' entries
-  static constexpr int SMEM = OFF_BAR + 16;                    // two mbarriers
-  static_assert(GPM % 128 == 0 && DGS % 128 == 0 && G1 % 128 == 0 && GOP % 128 == 0 && STATE % 128 == 0,
-                "TMA destinations on 128-byte boundaries");
+  static constexpr int STAGE = GPM + DGS + G1;                 // bytes, multiple of 128
+  static constexpr int NSTAGE = WENO_K1_STAGES;
+  static constexpr int SMEM = NSTAGE * STAGE + 16;             // stages + two mbarriers
 };
-
-// Candidate gradients and indicators of one (cell, variable) from the staged tile: hi / lo rows of
-// the cell (slot s at words 4 s .. 4 s + 3), its stencil entries raw[(s - 1) TILE] (walls only)
-// and gradient operators gop[j TILE].  Same arithmetic as cell_gradients.
-template <int M, int TILE, bool WALLS>
-__device__ __forceinline__ void staged_gradients(const float* hi, const float* lo, const int32_t* raw,
-                                                 const float4* gop, int v, float a0, float eps, float& w0,
-                                                 float& l0, CandPairs<(M + 1) / 2>& cp) {
-  w0 = hi[v];
-  l0 = lo[v];
-  float dW[M + 1];
-  dW[0] = 0.0f;
-  const int32_t fm = flip_mask<WALLS, 4>(v);
-#pragma unroll
-  for (int s = 1; s <= M; ++s) {
-    float a = hi[4 * s + v], b = lo[4 * s + v];
-    if (WALLS && (raw[(s - 1) * TILE] & fm)) { a = -a; b = -b; }
-    dW[s] = (a - w0) + (b - l0);
-  }
-  float gx[2 * ((M + 1) / 2)], gy[2 * ((M + 1) / 2)], b[2 * ((M + 1) / 2)];
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    const float da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
-    const float4 m = gop[j * TILE];
-    gx[j] = fmaf(m.x, da, m.y * db);
-    gy[j] = fmaf(m.z, da, m.w * db);
-    b[j] = a0 * fmaf(gx[j], gx[j], gy[j] * gy[j]);
-  }
-  if (M % 2) { gx[M] = 0.f; gy[M] = 0.f; b[M] = 0.f; }
-#pragma unroll
-  for (int k = 0; k < (M + 1) / 2; ++k) {
-    cp.gx[k] = f2(gx[2 * k], gx[2 * k + 1]);
-    cp.gy[k] = f2(gy[2 * k], gy[2 * k + 1]);
-    const float2 bb = f2(b[2 * k], b[2 * k + 1]);
-    cp.b[k] = bb;
-    cp.be[k] = __fadd2_rn(bb, f2(eps, eps));
-  }
-}
 
 template <int M, int G, bool WALLS>
 __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WENO_K1_TILE) k_reconstruct_tma(
     const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
-    const __grid_constant__ CUtensorMap map_g1, const __grid_constant__ CUtensorMap map_gop,
-    const float* __restrict__ U, const float* __restrict__ Ulo, const int32_t* __restrict__ slot,
-    const float* __restrict__ area, int64_t N, int64_t first, int64_t gbase, float* __restrict__ Wg, float eps,
-    int linear, int* __restrict__ err, int stall) {
+    const __grid_constant__ CUtensorMap map_g1, const float* __restrict__ U, const float* __restrict__ Ulo,
+    const int32_t* __restrict__ slot, const float4* __restrict__ gop4, const float* __restrict__ area, int64_t N,
+    int64_t pitch, int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, int linear,
+    int* __restrict__ err, int stall) {
   using L = TmaTile<M, G>;
-  constexpr int P = (M + 1) / 2, TILE = L::TILE;
+  constexpr int P = (M + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
-  float* sHi = reinterpret_cast<float*>(smem + L::OFF_HI);
-  float* sLo = reinterpret_cast<float*>(smem + L::OFF_LO);
-  int32_t* sRaw = reinterpret_cast<int32_t*>(smem + L::OFF_RAW);
-  const float4* sgp = reinterpret_cast<const float4*>(smem);
-  const float4* sds = reinterpret_cast<const float4*>(smem + L::GPM);
-  const float2* sg1 = reinterpret_cast<const float2*>(smem + L::GPM + L::DGS);
-  const float4* sgo = reinterpret_cast<const float4*>(smem + L::OFF_GOP);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);  // [0] weights, [1] gradient operators
-  const int tid = threadIdx.x, cl = tid >> 2, v = tid & 3;
-  const int64_t ntiles = (N + TILE - 1) / TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::NSTAGE * L::STAGE);
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (N + L::TILE - 1) / L::TILE;
   if (tid == 0) {
     // stall != 0 (testing aid): one arrival more than any thread makes, so the waits run out
     mbar_init(&bar[0], stall ? 2 : 1);
@@ -585,151 +546,89 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WE
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  auto issue_weights = [&](int64_t t) {
-    mbar_expect_tx(&bar[0], L::WTS);
-    tma_load_2d(smem, &map_gpm, (int)(t * TILE * 4), 0, &bar[0]);
-    tma_load_2d(smem + L::GPM, &map_dgs, (int)(t * TILE * 4), 0, &bar[0]);
-    if (M % 4) tma_load_2d(smem + L::GPM + L::DGS, &map_g1, (int)(t * TILE * 2), 0, &bar[0]);
-  };
-  auto issue_gop = [&](int64_t t) {
-    mbar_expect_tx(&bar[1], L::GOP);
-    tma_load_2d(smem + L::OFF_GOP, &map_gop, (int)(t * TILE * 4), 0, &bar[1]);
-  };
-  constexpr int RAWW = (L::RAW + 15) / 16 * 4;  // words per entries buffer
-  // stencil entries of tile t into entries buffer b: e -> slot e / TILE + 1 of cell e % TILE (-1 past N)
-  auto fetch_entries = [&](int64_t t, int b) {
-#pragma unroll
-    for (int k = 0; k < L::PER_THREAD; ++k) {
-      const int e = tid + L::THREADS * k;
-      if (e < M * TILE) {
-        const int64_t q = t * TILE + e % TILE;
-        if (q < N) cp_async4(sRaw + b * RAWW + e, slot + (int64_t)(e / TILE) * N + q);
-        else sRaw[b * RAWW + e] = -1;
-      }
-    }
-  };
-  // stencil states of tile t from the entries in buffer b
-  auto issue_states = [&](int64_t t, int b) {
-#pragma unroll
-    for (int k = 0; k < L::PER_THREAD; ++k) {
-      const int e = tid + L::THREADS * k;
-      const int32_t raw = e < M * TILE ? sRaw[b * RAWW + e] : -1;
-      if (raw >= 0) {
-        const int s = e / TILE + 1, c = e % TILE;
-        const int64_t cs = WALLS ? (raw & kDevSlotCell) : raw;
-        cp_async16(sHi + c * L::SW + 4 * s, U + cs * 4);
-        cp_async16(sLo + c * L::SW + 4 * s, Ulo + cs * 4);
-      }
-    }
-    if (tid < 2 * TILE) {  // the tile's own cells: hi rows by threads [0, TILE), lo rows by [TILE, 2 TILE)
-      const int c = tid % TILE;
-      const int64_t q = t * TILE + c;
-      if (q < N) cp_async16((tid < TILE ? sHi : sLo) + c * L::SW, (tid < TILE ? U : Ulo) + (first + q) * 4);
-    }
-  };
-  // on a timed-out wait: record it, let every copy this block started land, leave
-  auto give_up = [&](bool w0_pending, uint32_t p0, bool w1_pending, uint32_t p1) {
-    cp_async_wait_all();
-    if (tid == 0) {
-      *err = 1;
-      if (w0_pending) mbar_wait_bounded(&bar[0], p0);
-      if (w1_pending) mbar_wait_bounded(&bar[1], p1);
-    }
+  auto issue = [&](int64_t tile, int stage) {
+    unsigned char* base = smem + stage * L::STAGE;
+    mbar_expect_tx(&bar[stage], L::STAGE);
+    tma_load_2d(base, &map_gpm, (int)(tile * L::TILE * 4), 0, &bar[stage]);
+    tma_load_2d(base + L::GPM, &map_dgs, (int)(tile * L::TILE * 4), 0, &bar[stage]);
+    if (M % 4) tma_load_2d(base + L::GPM + L::DGS, &map_g1, (int)(tile * L::TILE * 2), 0, &bar[stage]);
   };
   int64_t tile = blockIdx.x;
-  float a_next = 0.f;
-  // prologue: the first tile's entries (needed at once), states and tables; the second tile's entries
-  if (tile < ntiles) {
-    if (tid == 0) {
-      issue_weights(tile);
-      issue_gop(tile);
+  if (tid == 0 && tile < ntiles) issue(tile, 0);
+  uint32_t phase[2] = {0u, 0u};
+  for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+    const int st = L::NSTAGE == 2 ? (i & 1) : 0;
+    const int64_t next = tile + gridDim.x;
+    if (L::NSTAGE == 2 && tid == 0 && next < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of that buffer
+      issue(next, st ^ 1);
     }
-    fetch_entries(tile, 0);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-    issue_states(tile, 0);
-    if (tile + gridDim.x < ntiles) fetch_entries(tile + gridDim.x, 1);
-    cp_async_commit();
-    const int64_t q = tile * TILE + cl;
-    a_next = q < N ? __ldg(area + first + q) : 0.f;
-  }
-  uint32_t phase = 0u;  // both barriers complete once per tile
-  for (int it = 0; tile < ntiles; tile += gridDim.x, phase ^= 1u, ++it) {
-    const int64_t next = tile + gridDim.x, next2 = next + gridDim.x;
-    const int b = it & 1;  // entries buffer of this tile; b ^ 1 holds the next tile's
-    const float a0 = a_next;
-    if (next < ntiles) {  // area of the next tile: consumed in the next iteration
-      const int64_t q = next * TILE + cl;
-      a_next = q < N ? __ldg(area + first + q) : 0.f;
-    }
-    cp_async_wait_all();  // this tile's states and the next tile's entries
-    const bool okg = mbar_wait_bounded(&bar[1], phase);
-    if (__syncthreads_or(!okg)) {
-      give_up(true, phase, false, 0u);
-      return;
-    }
-    const int64_t q = tile * TILE + cl;
+    const int64_t q = tile * L::TILE + (tid >> 2);
+    const int v = tid & 3;
+    // the stencil gathers do not depend on the staged tables: start them before waiting
     float w0 = 0.f, l0 = 0.f;
     CandPairs<P> cp;
-    if (q < N) staged_gradients<M, TILE, WALLS>(sHi + cl * L::SW, sLo + cl * L::SW, sRaw + b * RAWW + cl, sgo + cl,
-                                                v, a0, eps, w0, l0, cp);
-    __syncthreads();  // the tile's states, entries and gradient operators are read: stage the next tile's
-    if (next < ntiles) {
-      issue_states(next, b ^ 1);
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_gop(next);
-      }
+    if (q < N) {
+      const int64_t c = first + q;
+      cell_gradients<4, M, WALLS>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
     }
-    if (next2 < ntiles) fetch_entries(next2, b);
-    cp_async_commit();
-    const bool okw = mbar_wait_bounded(&bar[0], phase);
-    if (__syncthreads_or(!okw)) {
-      give_up(false, 0u, next < ntiles, phase ^ 1u);
+    const bool ok = mbar_wait_bounded(&bar[st], phase[st]);
+    phase[st] ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        *err = 1;
+        // drain the copy still headed for the other buffer before leaving
+        if (L::NSTAGE == 2 && next < ntiles) mbar_wait_bounded(&bar[st ^ 1], phase[st ^ 1]);
+      }
       return;
     }
     if (q < N) {
+      const unsigned char* base = smem + st * L::STAGE;
+      const float4* sgp = reinterpret_cast<const float4*>(base);
+      const float4* sds = reinterpret_cast<const float4*>(base + L::GPM);
+      const float2* sg1 = reinterpret_cast<const float2*>(base + L::GPM + L::DGS);
+      const int cl = tid >> 2;
       float* out = Wg + (gbase + q * G) * 4 + v;
       auto tables = [&](int g, float4& d, float2* gp, float2* gn) {
-        d = sds[g * TILE + cl];
+        d = sds[g * L::TILE + cl];
 #pragma unroll
         for (int k = 0; k < L::M4; ++k) {
-          const float4 x = sgp[(g * 2 * L::M4 + k) * TILE + cl];
-          const float4 y = sgp[(g * 2 * L::M4 + L::M4 + k) * TILE + cl];
+          const float4 x = sgp[(g * 2 * L::M4 + k) * L::TILE + cl];
+          const float4 y = sgp[(g * 2 * L::M4 + L::M4 + k) * L::TILE + cl];
           gp[2 * k] = f2(x.x, x.y); gp[2 * k + 1] = f2(x.z, x.w);
           gn[2 * k] = f2(y.x, y.y); gn[2 * k + 1] = f2(y.z, y.w);
         }
         if (M % 4) {
-          const float2 e = sg1[g * TILE + cl];
+          const float2 e = sg1[g * L::TILE + cl];
           gp[P - 1] = f2(e.x, 0.f);
           gn[P - 1] = f2(e.y, 0.f);
         }
       };
-      uint32_t redo = 0u;  // Gauss points whose weights left the FP32 range
+      float amin = 1.0f;  // smallest sum of alpha over the Gauss points
 #pragma unroll 1
       for (int g = 0; g < G; ++g) {
         float4 d;
         float2 gp[P], gn[P];
         tables(g, d, gp, gn);
-        bool r;
-        const float incr = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, r);
-        redo |= (uint32_t)r << g;
+        float am;
+        const float incr = gauss_increment<M>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, am);
+        amin = fminf(amin, am);
         out[(int64_t)g * 4] = w0 + (l0 + incr);
       }
+      if (!(amin >= kAlphaMin)) {  // weights outside the FP32 range (rare): every point again in FP64
 #pragma unroll 1
-      for (int g = 0; redo != 0u; ++g, redo >>= 1) {
-        if (!(redo & 1u)) continue;
-        float4 d;
-        float2 gp[P], gn[P];
-        tables(g, d, gp, gn);
-        out[(int64_t)g * 4] = w0 + (l0 + gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps));
+        for (int g = 0; g < G; ++g) {
+          float4 d;
+          float2 gp[P], gn[P];
+          tables(g, d, gp, gn);
+          out[(int64_t)g * 4] = w0 + (l0 + gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps));
+        }
       }
     }
-    __syncthreads();  // the weights buffer is free for the next tile's copy
-    if (tid == 0 && next < ntiles) {
+    __syncthreads();  // the buffer is free for the copy issued in the next iteration
+    if (L::NSTAGE == 1 && tid == 0 && next < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_weights(next);
+      issue(next, 0);
     }
   }
 }
@@ -1177,21 +1076,19 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
           gn[P - 1] = f2(e.y, 0.f);
         }
       };
-      float incr[2];
-      bool redo[2];
+      float incr[2], am[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const float4 d = h ? d1 : d0;
         float2 gp[P], gn[P];
         weights(2 * k + h, gp, gn);
-        incr[h] = gauss_increment<P>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, redo[h]);
+        incr[h] = gauss_increment<M>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, am[h]);
       }
       // weights outside the FP32 range: those lanes redo their points in FP64 before the
       // (converged) back-projection
-      if (redo[0] || redo[1]) {
+      if (!(fminf(am[0], am[1]) >= kAlphaMin)) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-          if (!redo[h]) continue;
           const float4 d = h ? d1 : d0;
           float2 gp[P], gn[P];
           weights(2 * k + h, gp, gn);

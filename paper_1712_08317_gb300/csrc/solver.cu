@@ -201,12 +201,12 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
       using TT = weno::dev::TmaTile<9, 6>;
       if (s.nQ && (which & 1))
         weno::dev::k_reconstruct_tma<12, 8, WALLS><<<tma_grid(s.k1q, s.nQ), TQ::THREADS, TQ::SMEM, st>>>(
-            s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
-            (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
+            s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
+            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       if (s.nT && (which & 2))
         weno::dev::k_reconstruct_tma<9, 6, WALLS><<<tma_grid(s.k1t, s.nT), TT::THREADS, TT::SMEM, st>>>(
-            s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
-            8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
+            s.t_map_gpm, s.t_map_dgs, s.t_map_g1, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
+            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
       return;
     }
   }
@@ -670,6 +670,9 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   // point whose linear weights are all >= 0 has sigma- = 0 and gamma- = 0 / 0
   if (!(p.eps > 0) || !(p.theta > 1) || (p.eqn == WENO_EQN_EULER && !(p.gas_gamma > 1)))
     return fail(WENO_EINVAL, "parameters out of range (eps > 0, theta > 1, gamma > 1)");
+  // FP32 weights: alpha = gamma / (beta~ + eps)^2 <= 1 / eps^2 stays far inside the FP32 range
+  if (p.precision == WENO_FP32C && !(p.eps >= 1e-15))
+    return fail(WENO_EINVAL, "FP32C solvers need eps >= 1e-15 (FP32 range of the nonlinear weights); use FP64");
   if (p.characteristic && p.eqn != WENO_EQN_EULER)
     return fail(WENO_EINVAL, "characteristic variables are defined for the Euler equations only");
   const bool walls = std::any_of(mesh->m.fwall.begin(), mesh->m.fwall.end(), [](int8_t w) { return w >= 0; });

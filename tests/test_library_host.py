@@ -179,3 +179,15 @@ def test_solver_create_rejects_theta_at_most_one(lib, theta):
     assert b"theta" in lib.weno_last_error()
     with pytest.raises(ValueError):
         Params(theta=theta)
+
+
+def test_fp32c_solver_needs_eps_of_at_least_1e_15(lib):
+    """FP32 nonlinear weights alpha = gamma / (beta~ + eps)^2 <= 1 / eps^2 must stay inside the FP32
+    range: FP32C solvers reject eps < 1e-15 (before any CUDA call); FP64 solvers take any eps > 0."""
+    from paper_1712_08317_gb300 import _capi
+    from paper_1712_08317_gb300.api import Mesh, params_struct
+    m = Mesh.from_input(S.mesh_for_config(1, n=6, seed=0))
+    h = ctypes.c_void_p()
+    p = params_struct(precision="fp32c", eps=1e-20)
+    assert lib.weno_solver_create(m._h, ctypes.byref(p), None, ctypes.byref(h)) == _capi.WENO_EINVAL
+    assert b"1e-15" in lib.weno_last_error()

@@ -120,8 +120,15 @@ def test_weighting_parameters_of_section_3_3():
 
 
 def test_optimisation_brings_large_weights_to_order_one():
-    """Tables 1-2: raw max|gamma| grows on poor meshes, the optimised maximum is O(1)."""
+    """Tables 1-2: raw max|gamma| grows on poor meshes (the paper's irregular meshes: 2.6e2-2.9e5), the
+    optimised maximum is O(1) (at most 8.56).  The paper's meshes are figures only, so the pin is
+    qualitative: on a low-quality synthetic mesh the raw weights exceed 10, the optimised ones stay
+    within 1.5 x the paper's largest optimised value, and the optimisation cuts the maximum at least
+    5-fold (the paper's tables: 30-fold or more on every irregular mesh)."""
+    raw_tab = np.loadtxt(__file__.replace("test_oracle_reconstruction.py", "golden/table1_max_gamma_raw.txt"))
     golden = np.loadtxt(__file__.replace("test_oracle_reconstruction.py", "golden/table2_max_gamma_opt.txt"))
+    irregular = [1, 3]
+    assert (raw_tab[:, irregular] / golden[:, irregular]).min() > 30.0   # the contrast the tables show
     mi = S.stretched_vortex_mesh(24, frac=0.5, delta=0.4, seed=2)
     groups = precompute(OracleMesh.from_input(mi), Params())
     raw = max(np.abs(t.gamma_raw).max() for t in groups)
