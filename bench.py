@@ -33,8 +33,8 @@ FALLBACK_HBM_GBS = 6800.0
 # k_reconstruct_tma on the 637k-cell mesh of the benchmark family (n = 700), divided by its cells of
 # each type.  They describe the kernel source they were captured on (SHA-256 of csrc/kernels.cuh);
 # for any other source the bench line reports traffic null.
-K1_TRAFFIC = {"kernels_cuh_sha256": "d679aebe3ecd0b9c3e312a1935736c67ae9f26fb327f12a6b8a01fbed75d053d",
-              "quad": 1306.7, "tri": 851.2}
+K1_TRAFFIC = {"kernels_cuh_sha256": "3d44ec2b88233e9f53ffbeeef02dc131bf364db692304c9c27349f983bda0e23",
+              "quad": 1305.5, "tri": 851.5}
 WORKLOAD_N = 1754
 
 

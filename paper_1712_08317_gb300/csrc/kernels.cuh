@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -975,15 +976,25 @@ struct CharTile {
   static constexpr int SMEM = STAGE + 16;                      // one buffer + one mbarrier (padded)
 };
 
-template <int M, int G, bool WALLS>
+// FIXUP = false: the pass, with FP32 weights; every tile writes redo[tile] = 1 if a Gauss point
+// of one of its cells left the FP32 range of the weights, else 0, and a tile so marked writes
+// cells[tile * TILE / 8 ...], one bit per cell, which of its cells did.  FIXUP = true: run right
+// after, it redoes those cells with the weights in FP64 (a separate instance keeps that code, and
+// its call, out of the pass's register allocation); the decision per cell keeps every cell's
+// result independent of which cells share its tile.  redo is 4-byte aligned and readable up to
+// the next multiple of 4 bytes past the last tile.
+constexpr int kFixupChunk = 128;  // tiles a warp scans with one 4-byte load per lane
+template <int M, int G, bool WALLS, bool FIXUP>
 __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 / WENO_K1_TILE)
     k_reconstruct_char_tma(const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
                            const __grid_constant__ CUtensorMap map_g1, const __grid_constant__ CUtensorMap map_gop,
                            const float* __restrict__ U, const float* __restrict__ Ulo,
                            const int32_t* __restrict__ slot, const float* __restrict__ area, int64_t N,
                            int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, float gas_gamma,
-                           int linear, int* __restrict__ err, int stall) {
+                           int linear, uint8_t* __restrict__ redo, uint8_t* __restrict__ cells,
+                           int* __restrict__ err, int stall) {
   using L = CharTile<M, G>;
+  static_assert(L::TILE % 8 == 0, "a byte of cell marks per 8 cells");
   constexpr int P = (M + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::STAGE);
@@ -1002,17 +1013,47 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
     if (M % 4) tma_load_2d(smem + L::GPM + L::DGS, &map_g1, (int)(tile * L::TILE * 2), 0, &bar[0]);
     tma_load_2d(smem + L::GPM + L::DGS + L::G1, &map_gop, (int)(tile * L::TILE * 4), 0, &bar[0]);
   };
-  int64_t tile = blockIdx.x;
-  if (tid == 0 && tile < ntiles) issue(tile);
+  // FIXUP: the block scans chunks blockIdx.x, + gridDim.x, ... of kFixupChunk marks; every warp
+  // reads the same words, so all warps walk the same sequence of marked tiles
+  int64_t chunk = (int64_t)blockIdx.x - gridDim.x;
+  uint32_t lanes = 0u, nib = 0u, mine = 0u;
+  int cur = 0;
+  auto next_marked = [&]() -> int64_t {
+    while (nib == 0u) {
+      while (lanes == 0u) {
+        chunk += gridDim.x;
+        if (chunk * kFixupChunk >= ntiles) return ntiles;
+        const int64_t t0 = chunk * kFixupChunk + 4 * (tid & 31);
+        const uint32_t v = t0 < ntiles ? *reinterpret_cast<const uint32_t*>(redo + t0) : 0u;
+        mine = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (t0 + j < ntiles && ((v >> (8 * j)) & 0xffu)) mine |= 1u << j;
+        lanes = __ballot_sync(0xffffffffu, mine != 0u);
+      }
+      cur = __ffs(lanes) - 1;
+      lanes &= lanes - 1u;
+      nib = __shfl_sync(0xffffffffu, mine, cur);
+    }
+    const int j = __ffs(nib) - 1;
+    nib &= nib - 1u;
+    return chunk * kFixupChunk + 4 * cur + j;
+  };
+  int64_t tile = FIXUP ? next_marked() : (int64_t)blockIdx.x;
+  if (!FIXUP && tid == 0 && tile < ntiles) issue(tile);
   uint32_t phase = 0u;
   const float4* sgp = reinterpret_cast<const float4*>(smem);
   const float4* sds = reinterpret_cast<const float4*>(smem + L::GPM);
   const float2* sg1 = reinterpret_cast<const float2*>(smem + L::GPM + L::DGS);
   const float4* sgo = reinterpret_cast<const float4*>(smem + L::GPM + L::DGS + L::G1);
-  for (; tile < ntiles; tile += gridDim.x) {
+  for (; tile < ntiles; tile = FIXUP ? next_marked() : tile + gridDim.x) {
+    if (FIXUP && tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the previous tile's reads
+      issue(tile);
+    }
     const int64_t next = tile + gridDim.x;
     const int64_t qr = tile * L::TILE + cl;
-    const bool act = qr < N;
+    const bool act = qr < N && (!FIXUP || ((cells[tile * (L::TILE / 8) + (cl >> 3)] >> (cl & 7)) & 1u));
     const int64_t q = act ? qr : N - 1;
     const int64_t c = first + q;
     // stencil gathers (independent of the staged tables) before the wait
@@ -1032,8 +1073,10 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
       if (tid == 0) *err = 1;
       return;
     }
-#pragma unroll 1
-    for (int k = 0; k < G / 2; ++k) {
+    // the Gauss points of face k in the frame of that face; FP64 = true evaluates the nonlinear
+    // weights in FP64 (the rare second pass), and returns the smallest sum of alpha otherwise
+    auto face = [&](int k, auto fp64_tag) -> float {
+      constexpr bool FP64 = decltype(fp64_tag)::value;
       float Wn[4];
       slot_state4<float, WALLS>(U, __ldg(slot + (int64_t)k * N + q), Wn);  // slot k+1: across face k
       const float4 d0 = sds[(2 * k) * L::TILE + cl], d1 = sds[(2 * k + 1) * L::TILE + cl];
@@ -1062,7 +1105,12 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
         cp.b[p] = f2(b[2 * p], b[2 * p + 1]);
         cp.be[p] = __fadd2_rn(cp.b[p], f2(eps, eps));
       }
-      auto weights = [&](int g, float2* gp, float2* gn) {
+      float amin = 1.0f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int g = 2 * k + h;
+        const float4 d = h ? d1 : d0;
+        float2 gp[P], gn[P];
 #pragma unroll
         for (int kk = 0; kk < L::M4; ++kk) {
           const float4 x = sgp[(g * 2 * L::M4 + kk) * L::TILE + cl];
@@ -1075,34 +1123,38 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
           gp[P - 1] = f2(e.x, 0.f);
           gn[P - 1] = f2(e.y, 0.f);
         }
-      };
-      float incr[2], am[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float4 d = h ? d1 : d0;
-        float2 gp[P], gn[P];
-        weights(2 * k + h, gp, gn);
-        incr[h] = gauss_increment<M>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, am[h]);
-      }
-      // weights outside the FP32 range: those lanes redo their points in FP64 before the
-      // (converged) back-projection
-      if (!(fminf(am[0], am[1]) >= kAlphaMin)) {
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          const float4 d = h ? d1 : d0;
-          float2 gp[P], gn[P];
-          weights(2 * k + h, gp, gn);
-          incr[h] = gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps);
+        float incr;
+        if constexpr (FP64) {
+          incr = act ? gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps) : 0.f;
+        } else {
+          float am;
+          incr = gauss_increment<M>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, am);
+          amin = fminf(amin, am);
         }
+        const float dWl = lane_sum4(Rr, incr, base);
+        if (act) Wg[(gbase + q * G + g) * 4 + l] = w0 + (l0 + dWl);
       }
+      return amin;
+    };
+    float amin = 1.0f;
+#pragma unroll 1
+    for (int k = 0; k < G / 2; ++k) amin = fminf(amin, face(k, std::integral_constant<bool, FIXUP>{}));
+    if constexpr (!FIXUP) {
+      // weights outside the FP32 range at a cell of the tile (rare): the fix-up pass redoes the
+      // cell (any of its four lanes; lanes 4c..4c+3 of warp w hold cell 8w + c).  Lanes past the
+      // end read the zero fill of the tables and are left out.
+      const uint32_t v = __ballot_sync(0xffffffffu, act && !(amin >= kAlphaMin));
+      const int need = __syncthreads_or(v != 0u);
+      if (need && (tid & 31) == 0) {
+        uint32_t m8 = 0u;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float dWl = lane_sum4(Rr, incr[h], base);
-        if (act) Wg[(gbase + q * G + 2 * k + h) * 4 + l] = w0 + (l0 + dWl);
+        for (int c8 = 0; c8 < 8; ++c8) m8 |= ((v >> (4 * c8)) & 0xfu) ? 1u << c8 : 0u;
+        cells[tile * (L::TILE / 8) + (tid >> 5)] = (uint8_t)m8;
       }
+      if (tid == 0) redo[tile] = (uint8_t)need;
     }
     __syncthreads();  // the buffer is free for the next tile's copy
-    if (tid == 0 && next < ntiles) {
+    if (!FIXUP && tid == 0 && next < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(next);
     }

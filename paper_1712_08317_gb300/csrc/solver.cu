@@ -101,6 +101,7 @@ struct weno_solver_s {
   CUtensorMap q_map_gpm{}, q_map_dgs{}, t_map_gpm{}, t_map_dgs{}, t_map_g1{};
   CUtensorMap q_map_gop{}, t_map_gop{};  // gradient operators
   int* err = nullptr;                 // set by a kernel whose bounded wait timed out
+  uint8_t* char_redo = nullptr;       // FP32C characteristic tiles whose weights left the FP32 range
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
   void *area = nullptr, *inv_area = nullptr, *inv_area_lo = nullptr;
   double* area64 = nullptr;
@@ -161,10 +162,28 @@ static_assert(weno::dev::kDevFlipX == weno::kFlipX && weno::dev::kDevFlipY == we
               "stencil table bit layout shared by the host tables and the kernels");
 
 // ------------------------------------------------------------ launches
+// Fix-up marks of the FP32C characteristic reconstruction, per cell group (quads, then
+// triangles): one byte per tile, then one bit per cell of the tile, each part padded to 16
+// bytes; zero bytes for every other path.
+int64_t redo_part(int64_t n) {
+  constexpr int64_t t = weno::dev::CharTile<12, 8>::TILE;
+  const int64_t tiles = (n + t - 1) / t;
+  return (tiles + 15) / 16 * 16 + (tiles * (t / 8) + 15) / 16 * 16;
+}
+int64_t redo_tiles_part(int64_t n) {
+  constexpr int64_t t = weno::dev::CharTile<12, 8>::TILE;
+  return ((n + t - 1) / t + 15) / 16 * 16;
+}
+int64_t redo_bytes(const S& s) {
+  if (s.fp64 || s.nv != 4 || !s.prm.characteristic) return 0;
+  return redo_part(s.nQ) + redo_part(s.nT);
+}
+
 // Cell reconstruction into the Gauss-value array wg.  which: bit 0 = quad group,
 // bit 1 = triangle group.
 template <typename T, int NV, bool COMP, bool WALLS>
-void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which) {
+void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which,
+                             uint8_t* redo) {
   const T* u = static_cast<const T*>(U);
   const T* ul = static_cast<const T*>(Ulo);
   const T eps = (T)s.prm.eps, th = (T)s.prm.theta;
@@ -174,14 +193,30 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
       if constexpr (COMP) {  // packed FP32C tables staged by TMA (setup_tma runs for every FP32C Euler solver)
         using CQ = weno::dev::CharTile<12, 8>;
         using CT = weno::dev::CharTile<9, 6>;
-        if (s.nQ && (which & 1))
-          weno::dev::k_reconstruct_char_tma<12, 8, WALLS><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
+        // each pass is followed by its fix-up pass over the tiles it marked (a few us when none is)
+        uint8_t* cells_q = redo + redo_tiles_part(s.nQ);
+        uint8_t* redo_t = redo + redo_part(s.nQ);
+        uint8_t* cells_t = redo_t + redo_tiles_part(s.nT);
+        auto fix_grid = [&](int64_t n) {
+          const int64_t chunks = ((n + CQ::TILE - 1) / CQ::TILE + weno::dev::kFixupChunk - 1) / weno::dev::kFixupChunk;
+          return (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, 4 * s.nsm));
+        };
+        if (s.nQ && (which & 1)) {
+          weno::dev::k_reconstruct_char_tma<12, 8, WALLS, false><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
               s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
-              (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
-        if (s.nT && (which & 2))
-          weno::dev::k_reconstruct_char_tma<9, 6, WALLS><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
+              (float*)wg, eps, gg, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
+          weno::dev::k_reconstruct_char_tma<12, 8, WALLS, true><<<fix_grid(s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
+              s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
+              (float*)wg, eps, gg, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
+        }
+        if (s.nT && (which & 2)) {
+          weno::dev::k_reconstruct_char_tma<9, 6, WALLS, false><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
               s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
-              8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, s.err, s.debug_stall);
+              8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
+          weno::dev::k_reconstruct_char_tma<9, 6, WALLS, true><<<fix_grid(s.nT), CT::THREADS, CT::SMEM, st>>>(
+              s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
+              8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
+        }
       } else {
         if (s.nQ && (which & 1))
           weno::dev::k_reconstruct_char<T, 12, 8, COMP, WALLS><<<grid_of(s.k1q, s.nQ * 4), s.k1q.block, 0, st>>>(
@@ -235,16 +270,17 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
 // Walls only change the stencil gathers (momentum flips of mirror images); meshes without
 // walls run kernels without that code.
 template <typename T, int NV, bool COMP>
-void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which) {
+void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cudaStream_t st, int which,
+                             uint8_t* redo) {
   if constexpr (NV == 4) {
-    if (s.walls) return launch_reconstruct_impl<T, NV, COMP, true>(s, U, Ulo, wg, st, which);
+    if (s.walls) return launch_reconstruct_impl<T, NV, COMP, true>(s, U, Ulo, wg, st, which, redo);
   }
-  launch_reconstruct_impl<T, NV, COMP, false>(s, U, Ulo, wg, st, which);
+  launch_reconstruct_impl<T, NV, COMP, false>(s, U, Ulo, wg, st, which, redo);
 }
 
 template <typename T, int NV, bool COMP>
 void launch_reconstruct(S& s, const void* U, const void* Ulo, cudaStream_t st, int which = 3) {
-  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, s.Wg, st, which);
+  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, s.Wg, st, which, s.char_redo);
 }
 
 // Face fluxes of the Gauss values wg into fl; c places the stage in the step (time t + c dt).
@@ -494,9 +530,15 @@ int setup_tma(S& s) {
   if (s.nT && (r = make_map_2d(enc, &s.t_map_gop, s.t_gop, 4 * s.t_pitch, 9, 16 * s.t_pitch, 4 * kTile, 9)))
     return r;
   if (s.prm.characteristic) {
-    for (auto fn : {weno::dev::k_reconstruct_char_tma<12, 8, false>, weno::dev::k_reconstruct_char_tma<12, 8, true>})
+    for (auto fn : {weno::dev::k_reconstruct_char_tma<12, 8, false, false>,
+                    weno::dev::k_reconstruct_char_tma<12, 8, true, false>,
+                    weno::dev::k_reconstruct_char_tma<12, 8, false, true>,
+                    weno::dev::k_reconstruct_char_tma<12, 8, true, true>})
       CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::CharTile<12, 8>::SMEM));
-    for (auto fn : {weno::dev::k_reconstruct_char_tma<9, 6, false>, weno::dev::k_reconstruct_char_tma<9, 6, true>})
+    for (auto fn : {weno::dev::k_reconstruct_char_tma<9, 6, false, false>,
+                    weno::dev::k_reconstruct_char_tma<9, 6, true, false>,
+                    weno::dev::k_reconstruct_char_tma<9, 6, false, true>,
+                    weno::dev::k_reconstruct_char_tma<9, 6, true, true>})
       CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::CharTile<9, 6>::SMEM));
   }
   s.tma = true;
@@ -860,6 +902,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   CK(cudaMemsetAsync(d.flag, 0, sizeof(int) * d.n_inst, st));
   if ((r = d.alloc(&d.err, sizeof(int)))) return r;
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), st));
+  if (redo_bytes(d) && (r = d.alloc(&d.char_redo, (size_t)redo_bytes(d)))) return r;
   if (!d.fp64 && d.nv == 4 && (r = setup_tma(d))) return r;
   CK(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
   CK(cudaStreamSynchronize(st));
@@ -1147,8 +1190,9 @@ int static_scratch_base(int dev, void** base) {
 }
 
 template <typename T, int NV, bool COMP>
-void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void* wg, void* fl, cudaStream_t st) {
-  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, wg, st, 3);
+void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void* wg, void* fl, uint8_t* redo,
+                            cudaStream_t st) {
+  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, wg, st, 3, redo);
   launch_face_into<T, NV>(s, wg, fl, 0.0, st);
   if (s.nQ)
     weno::dev::k_gather<T, NV, 4, COMP, 0><<<grid_of(s.k3q, s.nQ), s.k3q.block, 0, st>>>(
@@ -1164,10 +1208,12 @@ void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void*
 
 extern "C" int weno_residual_static(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream) {
   if (!s || !U || !R || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
-  // Gauss-point values first, face fluxes after them on a 256-byte boundary
+  // Gauss-point values first, face fluxes after them on a 256-byte boundary, then (FP32C
+  // characteristic solvers) the reconstruction's fix-up marks, a byte per tile and a bit per cell
   const size_t wg_bytes = (size_t)(8 * s->nQ + 6 * s->nT) * s->nv * s->esz;
   const size_t f_off = (wg_bytes + 255) / 256 * 256;
-  const size_t need = f_off + (size_t)s->nF * s->nv * s->esz;
+  const size_t r_off = (f_off + (size_t)s->nF * s->nv * s->esz + 255) / 256 * 256;
+  const size_t need = r_off + (size_t)redo_bytes(*s);
   if (need > kStaticScratchBytes)
     return fail(WENO_EINVAL, "mesh too large for weno_residual_static: needs " + std::to_string(need) +
                                  " bytes of scratch, the fixed array holds " + std::to_string(kStaticScratchBytes));
@@ -1176,6 +1222,6 @@ extern "C" int weno_residual_static(weno_solver_t s, const void* U, const void* 
   int r = static_scratch_base(s->dev, &base);
   if (r) return r;
   unsigned char* b = static_cast<unsigned char*>(base);
-  WENO_DISPATCH(*s, launch_residual_static, *s, U, U_lo, R, b, b + f_off, (cudaStream_t)cuda_stream);
+  WENO_DISPATCH(*s, launch_residual_static, *s, U, U_lo, R, b, b + f_off, b + r_off, (cudaStream_t)cuda_stream);
   return check_launch();
 }

@@ -499,22 +499,32 @@ def test_batched_instances_with_inflow_keep_their_own_time():
     assert t[0] == dts[0] + dts[0] + dts[0] + dts[0] and t[1] == dts[1] + dts[1] + dts[1] + dts[1]
 
 
-@pytest.mark.parametrize("shape,size", [("ramp", 1e5), ("ramp", 1e7), ("step", 1e4), ("step", 1e5)])
-def test_fp32c_weights_stay_finite_at_huge_indicators(shape, size):
+@pytest.mark.parametrize("characteristic", [False, True])
+@pytest.mark.parametrize("shape,size", [("ramp", 1e5), ("ramp", 1e7), ("step", 1e4), ("step", 1e5),
+                                        ("rho_ramp", 1e5), ("rho_ramp", 1e7)])
+def test_fp32c_weights_stay_finite_at_huge_indicators(shape, size, characteristic):
     """Section 3.4's alpha = gamma / (beta~ + eps)^2 with beta~ ~ gamma^2 beta^3: a steep pressure
     ramp makes every candidate's beta ~ 1e8-1e12, so (beta~ + eps)^2 overflows FP32 and every alpha
-    of a group flushes to zero; a strong step puts such indicators next to smooth candidates.  The
-    FP32C path must still match the oracle (FP64) to FP32 accuracy, with no NaN."""
+    of a group flushes to zero; a strong step puts such indicators next to smooth candidates.  In
+    characteristic variables an isentropic-like pressure ramp projects to O(1) differences
+    (dp / c^2), so an isothermal density ramp (p = rho, moving at Mach ~0.9: the entropy field
+    carries (1 - 1/gamma) d rho) does the same there, and most cells take the FP64 fix-up.  The
+    FP32C path (component-wise and characteristic) must still match the oracle (FP64) to FP32
+    accuracy, with no NaN."""
     mi = S.mesh_for_config(3, n=14, seed=2, kind="mixed")
     om = OracleMesh.from_input(mi)
     cen = om.centroid
+    rho, u, v = np.ones(len(cen)), np.zeros(len(cen)), np.zeros(len(cen))
     if shape == "ramp":
         p = 1.0 + size * (cen[:, 0] + 0.3 * cen[:, 1])
-    else:
+    elif shape == "step":
         p = np.where(cen[:, 0] + 0.3 * cen[:, 1] < 0.55, size, 1.0)
-    W = S.euler_prim_to_cons(np.ones_like(p), 0.0 * p, 0.0 * p, p, 1.4)
-    ref = OracleSolver(om, Params()).residual(W)
-    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c")
+    else:
+        rho = 1.0 + size * (cen[:, 0] + 0.3 * cen[:, 1])
+        p, u, v = rho, u + 1.0, v + 0.5
+    W = S.euler_prim_to_cons(rho, u, v, p, 1.4)
+    ref = OracleSolver(om, Params(characteristic=characteristic)).residual(W)
+    sol = Solver(Mesh.from_input(mi), eqn="euler", precision="fp32c", characteristic=characteristic)
     U, Ul = sol.to_device(W)
     Rd = sol.residual(U, Ul)
     assert bool(torch.isfinite(Rd).all())
