@@ -455,14 +455,13 @@ __global__ void __launch_bounds__(256, WENO_K1_MIN_BLOCKS) k_reconstruct_f32c(
 // ---------------------------------------------------------------- K1 with TMA-staged tables
 // Euler FP32C, one block per tile or persistent: a tile is TILE consecutive cells of one type,
 // one (cell, variable) per thread.  One elected thread loads the tile's split
-// linear weights and Gauss offsets into shared memory with 2D TMA copies
-// (cp.async.bulk.tensor) completing on an mbarrier; the stencil gathers of the
-// tile are issued before the wait.  With one buffer (default) the next tile's
-// copy starts when the block has finished reading the current one and the
-// other resident block hides its latency, which leaves more of the unified
-// L1 to the gathers than two buffers would; WENO_K1_STAGES=2 prefetches the
-// next tile instead.  Every wait is bounded: on timeout the block records
-// *err = 1, drains its copies (bounded) and exits.
+// linear weights, Gauss offsets and gradient operators into shared memory with
+// 2D TMA copies (cp.async.bulk.tensor) completing on an mbarrier; the stencil
+// gathers of the tile are issued before the wait.  The next tile's copy starts
+// when the block has finished reading the current one, and the other resident
+// blocks hide its latency.  Every wait is bounded: on timeout the block
+// records *err = 1 and exits (its one copy has completed or is abandoned with
+// the block's shared memory).
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -509,127 +508,280 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 #endif
 static_assert(WENO_K1_TILE == 8 || WENO_K1_TILE == 16 || WENO_K1_TILE == 32 || WENO_K1_TILE == 64, "tile of 8, 16, 32 or 64 cells");
 
-#ifndef WENO_K1_STAGES
-#define WENO_K1_STAGES 1  // shared-memory table buffers per block (2: prefetch the next tile while computing)
-#endif
+constexpr int kFixupChunk = 128;  // tiles a warp of a fix-up pass scans with one 4-byte load per lane
 
-template <int M, int G>
-struct TmaTile {
-  static constexpr int TILE = WENO_K1_TILE;  // cells per tile; TILE x 4 threads (one per variable)
-  static constexpr int THREADS = TILE * 4;
-  static constexpr int M4 = M / 4;
-  static constexpr int GPM = G * 2 * M4 * TILE * 16;          // gamma+ rows then gamma- rows
-  static constexpr int DGS = G * TILE * 16;                    // (x_G - c0, sigma+, sigma-)
-  static constexpr int G1 = (M % 4) ? G * TILE * 8 : 0;        // (gamma+_8, gamma-_8) of triangles
-  static constexpr int STAGE = GPM + DGS + G1;                 // bytes, multiple of 128
-  static constexpr int NSTAGE = WENO_K1_STAGES;
-  static constexpr int SMEM = NSTAGE * STAGE + 16;             // stages + two mbarriers
+// The tiles a fix-up pass redoes, in the order it walks them: chunks blockIdx.x, + gridDim.x, ...
+// of kFixupChunk one-byte marks written by the pass before it.  Every warp of the block reads the
+// same words, so all warps walk the same sequence; next() returns ntiles at the end.  The marks
+// are 4-byte aligned and readable up to the next multiple of 4 bytes past the last tile.
+struct MarkScan {
+  const uint8_t* redo;
+  int64_t ntiles, chunk;
+  uint32_t lanes = 0u, nib = 0u, mine = 0u;
+  int cur = 0;
+  __device__ MarkScan(const uint8_t* r, int64_t n) : redo(r), ntiles(n), chunk((int64_t)blockIdx.x - gridDim.x) {}
+  __device__ int64_t next() {
+    while (nib == 0u) {
+      while (lanes == 0u) {
+        chunk += gridDim.x;
+        if (chunk * kFixupChunk >= ntiles) return ntiles;
+        const int64_t t0 = chunk * kFixupChunk + 4 * (threadIdx.x & 31);
+        const uint32_t w = t0 < ntiles ? *reinterpret_cast<const uint32_t*>(redo + t0) : 0u;
+        mine = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (t0 + j < ntiles && ((w >> (8 * j)) & 0xffu)) mine |= 1u << j;
+        lanes = __ballot_sync(0xffffffffu, mine != 0u);
+      }
+      cur = __ffs(lanes) - 1;
+      lanes &= lanes - 1u;
+      nib = __shfl_sync(0xffffffffu, mine, cur);
+    }
+    const int j = __ffs(nib) - 1;
+    nib &= nib - 1u;
+    return chunk * kFixupChunk + 4 * cur + j;
+  }
 };
 
-template <int M, int G, bool WALLS>
+// Marks of a pass whose lanes 4c..4c+3 of warp w hold cell 8w + c of a TILE-cell tile: redo[tile]
+// = 1 if a lane of the tile has `bad` set, else 0; a marked tile also writes one bit per cell to
+// cells[tile * TILE / 8 ...].  Called by every thread of the block.
+template <int TILE>
+__device__ __forceinline__ void write_marks(bool bad, int64_t tile, uint8_t* __restrict__ redo,
+                                            uint8_t* __restrict__ cells) {
+  const uint32_t v = __ballot_sync(0xffffffffu, bad);
+  const int need = __syncthreads_or(v != 0u);
+  if (need && (threadIdx.x & 31) == 0) {
+    uint32_t m8 = 0u;
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) m8 |= ((v >> (4 * c8)) & 0xfu) ? 1u << c8 : 0u;
+    cells[tile * (TILE / 8) + (threadIdx.x >> 5)] = (uint8_t)m8;
+  }
+  if (threadIdx.x == 0) redo[tile] = (uint8_t)need;
+}
+
+// Tables of the Euler FP32C reconstruction, staged per tile: the G Gauss points of a cell are taken
+// as G/2 pairs (the two points of one face), whose values share a float2.  Rows of TILE float4:
+//   gam [k][j]  (gamma+_j, gamma+_j', gamma-_j, gamma-_j') at points 2k and 2k+1 (split, normalised)
+//   dg  [2k]    (dx, dx', dy, dy')    x_G - c0 of the two points
+//   dg  [2k+1]  (sigma+, sigma+', sigma-, sigma-')
+//   gop [j]     D_j^+ (the 2x2 operator from the sub-stencil's differences to the gradient)
+template <int M, int G>
+struct PairTile {
+  static constexpr int TILE = WENO_K1_TILE;  // cells per tile; TILE x 4 threads (one per variable)
+  static constexpr int THREADS = TILE * 4;
+  static constexpr int NP = G / 2;
+  static constexpr int GAM = NP * M * TILE * 16;
+  static constexpr int DG = G * TILE * 16;
+  static constexpr int GOP = M * TILE * 16;
+  static constexpr int STAGE = GAM + DG + GOP;  // bytes, multiple of 128
+  static constexpr int SMEM = STAGE + 16;       // one buffer + one mbarrier (padded)
+};
+
+// Indicators are clamped to kBetaMax before beta^2 and beta^3 are formed (below).  A candidate
+// with beta that large has alpha = gamma / (beta~ + eps)^2 < 1e-40 whether clamped or not, i.e.
+// zero in FP32; where every candidate of a group is that large, the sum of alpha is zero and the
+// cell goes to the FP64 fix-up, which uses the unclamped value.
+constexpr float kBetaMax = 1e12f;
+
+// All G Gauss values of one (cell, variable) from its stencil differences dW (dW[0] = 0) and the
+// tile's tables, FP32 arithmetic (Sections 3.1-3.4):
+//   g_j = D_j^+ (dW_a, dW_b),  beta_j = |Omega| |g_j|^2,  p_j = g_j . (x_G - c0) = P^1_j(x_G) - W0,
+//   beta~+-_j + eps = beta (1 + q + q^2) + eps, q = gamma+-_j beta, evaluated as the polynomial
+//   (beta + eps) + gamma (beta^2 + gamma beta^3) in gamma,
+//   alpha+-_j = gamma+-_j / (beta~+-_j + eps)^2,
+//   R - W0 = sigma+ sum alpha+ p / sum alpha+  -  sigma- sum alpha- p / sum alpha-
+// (the linear scheme: sigma+ sum gamma+ p - sigma- sum gamma- p).  Candidates are the outer loop,
+// and the two points of a face share the paired FP32 instructions, so the per-point sums are the
+// only state kept across candidates.  Returns false if a sum of alpha fell below kAlphaMin (or is
+// not a number): the caller then has the cell redone with FP64 weights.
+template <int M, int G>
+__device__ __forceinline__ bool pair_points(const float4* __restrict__ sgam, const float4* __restrict__ sdg,
+                                            const float4* __restrict__ sgo, int cl, const float* dW, float a0,
+                                            float eps, int linear, float w0, float l0, float* __restrict__ out) {
+  constexpr int NP = G / 2, TILE = WENO_K1_TILE;
+  float2 dx[NP], dy[NP], Ap[NP], Bp[NP], Am[NP], Bm[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const float4 r = sdg[(2 * k) * TILE + cl];
+    dx[k] = f2(r.x, r.y);
+    dy[k] = f2(r.z, r.w);
+    Ap[k] = f2(0.f, 0.f); Bp[k] = f2(0.f, 0.f);
+    Am[k] = f2(0.f, 0.f); Bm[k] = f2(0.f, 0.f);
+  }
+  if (linear) {
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float4 m = sgo[j * TILE + cl];
+      const float da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
+      const float gx = fmaf(m.x, da, m.y * db), gy = fmaf(m.z, da, m.w * db);
+      const float2 GX = f2(gx, gx), GY = f2(gy, gy);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const float4 g4 = sgam[(k * M + j) * TILE + cl];
+        const float2 p = __ffma2_rn(GX, dx[k], __fmul2_rn(GY, dy[k]));
+        Bp[k] = __ffma2_rn(f2(g4.x, g4.y), p, Bp[k]);
+        Bm[k] = __ffma2_rn(f2(g4.z, g4.w), p, Bm[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const float4 s = sdg[(2 * k + 1) * TILE + cl];
+      out[(2 * k) * 4] = w0 + (l0 + (s.x * Bp[k].x - s.z * Bm[k].x));
+      out[(2 * k + 1) * 4] = w0 + (l0 + (s.y * Bp[k].y - s.w * Bm[k].y));
+    }
+    return true;
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float4 m = sgo[j * TILE + cl];
+    const float da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
+    const float gx = fmaf(m.x, da, m.y * db), gy = fmaf(m.z, da, m.w * db);
+    const float b = fminf(a0 * fmaf(gx, gx, gy * gy), kBetaMax);
+    const float b2 = b * b, b3 = b2 * b, be = b + eps;
+    const float2 GX = f2(gx, gx), GY = f2(gy, gy), C0 = f2(be, be), C1 = f2(b2, b2), C2 = f2(b3, b3);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const float4 g4 = sgam[(k * M + j) * TILE + cl];
+      const float2 gp = f2(g4.x, g4.y), gn = f2(g4.z, g4.w);
+      const float2 p = __ffma2_rn(GX, dx[k], __fmul2_rn(GY, dy[k]));
+      const float2 dp = __ffma2_rn(gp, __ffma2_rn(gp, C2, C1), C0);  // beta~+ + eps at both points
+      const float2 dn = __ffma2_rn(gn, __ffma2_rn(gn, C2, C1), C0);
+      const float2 ap = __fmul2_rn(gp, rcp2(__fmul2_rn(dp, dp)));
+      const float2 an = __fmul2_rn(gn, rcp2(__fmul2_rn(dn, dn)));
+      Ap[k] = __fadd2_rn(Ap[k], ap);
+      Bp[k] = __ffma2_rn(ap, p, Bp[k]);
+      Am[k] = __fadd2_rn(Am[k], an);
+      Bm[k] = __ffma2_rn(an, p, Bm[k]);
+    }
+  }
+  // Above kAlphaMin every candidate that matters is far from both FP32 limits; the sums never
+  // exceed 1 / eps^2 <= 1e30, since eps >= 1e-15 for FP32 weights.
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const float4 s = sdg[(2 * k + 1) * TILE + cl];
+    ok = ok && Ap[k].x >= kAlphaMin && Ap[k].y >= kAlphaMin && Am[k].x >= kAlphaMin && Am[k].y >= kAlphaMin;
+    const float i0 = s.x * Bp[k].x * rcp_approx(Ap[k].x) - s.z * Bm[k].x * rcp_approx(Am[k].x);
+    const float i1 = s.y * Bp[k].y * rcp_approx(Ap[k].y) - s.w * Bm[k].y * rcp_approx(Am[k].y);
+    out[(2 * k) * 4] = w0 + (l0 + i0);
+    out[(2 * k + 1) * 4] = w0 + (l0 + i1);
+  }
+  return ok;
+}
+
+// pair_points with the nonlinear weights in FP64 (IEEE division, indicators unclamped), whose
+// range holds every finite FP32 beta: the fix-up of cells whose FP32 sums of alpha left the
+// range.  Gauss points are the outer loop here, so only four sums are live.
+template <int M, int G>
+__device__ __forceinline__ void pair_points_fp64(const float4* __restrict__ sgam, const float4* __restrict__ sdg,
+                                                 const float4* __restrict__ sgo, int cl, const float* dW, float a0,
+                                                 float eps, float w0, float l0, float* __restrict__ out) {
+  constexpr int TILE = WENO_K1_TILE;
+#pragma unroll 1
+  for (int g = 0; g < G; ++g) {
+    const int k = g >> 1, h = g & 1;
+    const float4 r = sdg[(2 * k) * TILE + cl], s = sdg[(2 * k + 1) * TILE + cl];
+    const float dxg = h ? r.y : r.x, dyg = h ? r.w : r.z;
+    double Ap = 0.0, Bp = 0.0, Am = 0.0, Bm = 0.0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float4 m = sgo[j * TILE + cl];
+      const float da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
+      const float gx = fmaf(m.x, da, m.y * db), gy = fmaf(m.z, da, m.w * db);
+      const double b = (double)a0 * ((double)gx * gx + (double)gy * gy);
+      const double p = fmaf(gx, dxg, gy * dyg);
+      const float4 g4 = sgam[(k * M + j) * TILE + cl];
+      const double gp = h ? g4.y : g4.x, gn = h ? g4.w : g4.z;
+      const double qp = gp * b, qn = gn * b;
+      const double dp = b * (1.0 + qp + qp * qp) + eps, dn = b * (1.0 + qn + qn * qn) + eps;
+      const double ap = gp / (dp * dp), an = gn / (dn * dn);
+      Ap += ap;
+      Bp += ap * p;
+      Am += an;
+      Bm += an * p;
+    }
+    const double sp = h ? s.y : s.x, sm = h ? s.w : s.z;
+    out[g * 4] = w0 + (l0 + (float)(sp * (Bp / Ap) - sm * (Bm / Am)));
+  }
+}
+
+// FIXUP = false: the pass over every tile, FP32 weights (pair_points); each tile writes its marks
+// (write_marks) for the cells whose sums of alpha left the FP32 range.  FIXUP = true: run right
+// after on the marked tiles only (MarkScan), it redoes the marked cells with FP64 weights; the
+// decision per cell keeps every cell's result independent of which cells share its tile.
+template <int M, int G, bool WALLS, bool FIXUP>
 __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WENO_K1_TILE) k_reconstruct_tma(
-    const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
-    const __grid_constant__ CUtensorMap map_g1, const float* __restrict__ U, const float* __restrict__ Ulo,
-    const int32_t* __restrict__ slot, const float4* __restrict__ gop4, const float* __restrict__ area, int64_t N,
-    int64_t pitch, int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, int linear,
+    const __grid_constant__ CUtensorMap map_gam, const __grid_constant__ CUtensorMap map_dg,
+    const __grid_constant__ CUtensorMap map_gop, const float* __restrict__ U, const float* __restrict__ Ulo,
+    const int32_t* __restrict__ slot, const float* __restrict__ area, int64_t N, int64_t first, int64_t gbase,
+    float* __restrict__ Wg, float eps, int linear, uint8_t* __restrict__ redo, uint8_t* __restrict__ cells,
     int* __restrict__ err, int stall) {
-  using L = TmaTile<M, G>;
-  constexpr int P = (M + 1) / 2;
+  using L = PairTile<M, G>;
+  static_assert(L::TILE % 8 == 0, "a byte of cell marks per 8 cells");
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::NSTAGE * L::STAGE);
-  const int tid = threadIdx.x;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::STAGE);
+  const int tid = threadIdx.x, cl = tid >> 2, v = tid & 3;
   const int64_t ntiles = (N + L::TILE - 1) / L::TILE;
   if (tid == 0) {
-    // stall != 0 (testing aid): one arrival more than any thread makes, so the waits run out
-    mbar_init(&bar[0], stall ? 2 : 1);
-    mbar_init(&bar[1], stall ? 2 : 1);
+    mbar_init(&bar[0], stall ? 2 : 1);  // stall != 0 (testing aid): the wait runs out
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  auto issue = [&](int64_t tile, int stage) {
-    unsigned char* base = smem + stage * L::STAGE;
-    mbar_expect_tx(&bar[stage], L::STAGE);
-    tma_load_2d(base, &map_gpm, (int)(tile * L::TILE * 4), 0, &bar[stage]);
-    tma_load_2d(base + L::GPM, &map_dgs, (int)(tile * L::TILE * 4), 0, &bar[stage]);
-    if (M % 4) tma_load_2d(base + L::GPM + L::DGS, &map_g1, (int)(tile * L::TILE * 2), 0, &bar[stage]);
+  auto issue = [&](int64_t tile) {
+    mbar_expect_tx(&bar[0], L::STAGE);
+    tma_load_2d(smem, &map_gam, (int)(tile * L::TILE * 4), 0, &bar[0]);
+    tma_load_2d(smem + L::GAM, &map_dg, (int)(tile * L::TILE * 4), 0, &bar[0]);
+    tma_load_2d(smem + L::GAM + L::DG, &map_gop, (int)(tile * L::TILE * 4), 0, &bar[0]);
   };
-  int64_t tile = blockIdx.x;
-  if (tid == 0 && tile < ntiles) issue(tile, 0);
-  uint32_t phase[2] = {0u, 0u};
-  for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
-    const int st = L::NSTAGE == 2 ? (i & 1) : 0;
+  MarkScan scan(redo, ntiles);
+  int64_t tile = FIXUP ? scan.next() : (int64_t)blockIdx.x;
+  if (!FIXUP && tid == 0 && tile < ntiles) issue(tile);
+  uint32_t phase = 0u;
+  const float4* sgam = reinterpret_cast<const float4*>(smem);
+  const float4* sdg = reinterpret_cast<const float4*>(smem + L::GAM);
+  const float4* sgo = reinterpret_cast<const float4*>(smem + L::GAM + L::DG);
+  for (; tile < ntiles; tile = FIXUP ? scan.next() : tile + gridDim.x) {
+    if (FIXUP && tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the previous tile's reads
+      issue(tile);
+    }
     const int64_t next = tile + gridDim.x;
-    if (L::NSTAGE == 2 && tid == 0 && next < ntiles) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic reads of that buffer
-      issue(next, st ^ 1);
-    }
-    const int64_t q = tile * L::TILE + (tid >> 2);
-    const int v = tid & 3;
-    // the stencil gathers do not depend on the staged tables: start them before waiting
-    float w0 = 0.f, l0 = 0.f;
-    CandPairs<P> cp;
-    if (q < N) {
+    const int64_t q = tile * L::TILE + cl;
+    const bool act = q < N && (!FIXUP || ((cells[tile * (L::TILE / 8) + (cl >> 3)] >> (cl & 7)) & 1u));
+    // stencil gathers (independent of the staged tables) before the wait
+    float w0 = 0.f, l0 = 0.f, a0 = 0.f, dW[M + 1];
+    dW[0] = 0.f;
+    if (act) {
       const int64_t c = first + q;
-      cell_gradients<4, M, WALLS>(U, Ulo, slot, N, gop4, pitch, q, c, v, __ldg(area + c), eps, w0, l0, cp);
+      w0 = __ldg(U + c * 4 + v);
+      l0 = __ldg(Ulo + c * 4 + v);
+      const int32_t fm = flip_mask<WALLS, 4>(v);
+#pragma unroll
+      for (int s = 1; s <= M; ++s)
+        dW[s] = slot_delta<float, 4, WALLS, true>(U, Ulo, __ldg(slot + (int64_t)(s - 1) * N + q), v, fm, w0, l0);
+      a0 = __ldg(area + c);
     }
-    const bool ok = mbar_wait_bounded(&bar[st], phase[st]);
-    phase[st] ^= 1u;
+    const bool ok = mbar_wait_bounded(&bar[0], phase);
+    phase ^= 1u;
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        *err = 1;
-        // drain the copy still headed for the other buffer before leaving
-        if (L::NSTAGE == 2 && next < ntiles) mbar_wait_bounded(&bar[st ^ 1], phase[st ^ 1]);
-      }
+      if (tid == 0) *err = 1;
       return;
     }
-    if (q < N) {
-      const unsigned char* base = smem + st * L::STAGE;
-      const float4* sgp = reinterpret_cast<const float4*>(base);
-      const float4* sds = reinterpret_cast<const float4*>(base + L::GPM);
-      const float2* sg1 = reinterpret_cast<const float2*>(base + L::GPM + L::DGS);
-      const int cl = tid >> 2;
+    bool bad = false;
+    if (act) {
       float* out = Wg + (gbase + q * G) * 4 + v;
-      auto tables = [&](int g, float4& d, float2* gp, float2* gn) {
-        d = sds[g * L::TILE + cl];
-#pragma unroll
-        for (int k = 0; k < L::M4; ++k) {
-          const float4 x = sgp[(g * 2 * L::M4 + k) * L::TILE + cl];
-          const float4 y = sgp[(g * 2 * L::M4 + L::M4 + k) * L::TILE + cl];
-          gp[2 * k] = f2(x.x, x.y); gp[2 * k + 1] = f2(x.z, x.w);
-          gn[2 * k] = f2(y.x, y.y); gn[2 * k + 1] = f2(y.z, y.w);
-        }
-        if (M % 4) {
-          const float2 e = sg1[g * L::TILE + cl];
-          gp[P - 1] = f2(e.x, 0.f);
-          gn[P - 1] = f2(e.y, 0.f);
-        }
-      };
-      float amin = 1.0f;  // smallest sum of alpha over the Gauss points
-#pragma unroll 1
-      for (int g = 0; g < G; ++g) {
-        float4 d;
-        float2 gp[P], gn[P];
-        tables(g, d, gp, gn);
-        float am;
-        const float incr = gauss_increment<M>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, am);
-        amin = fminf(amin, am);
-        out[(int64_t)g * 4] = w0 + (l0 + incr);
-      }
-      if (!(amin >= kAlphaMin)) {  // weights outside the FP32 range (rare): every point again in FP64
-#pragma unroll 1
-        for (int g = 0; g < G; ++g) {
-          float4 d;
-          float2 gp[P], gn[P];
-          tables(g, d, gp, gn);
-          out[(int64_t)g * 4] = w0 + (l0 + gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps));
-        }
-      }
+      if constexpr (FIXUP)
+        pair_points_fp64<M, G>(sgam, sdg, sgo, cl, dW, a0, eps, w0, l0, out);
+      else
+        bad = !pair_points<M, G>(sgam, sdg, sgo, cl, dW, a0, eps, linear, w0, l0, out);
     }
-    __syncthreads();  // the buffer is free for the copy issued in the next iteration
-    if (L::NSTAGE == 1 && tid == 0 && next < ntiles) {
+    if constexpr (!FIXUP) write_marks<L::TILE>(bad, tile, redo, cells);
+    __syncthreads();  // the buffer is free for the next tile's copy
+    if (!FIXUP && tid == 0 && next < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(next, 0);
+      issue(next);
     }
   }
 }
@@ -976,14 +1128,11 @@ struct CharTile {
   static constexpr int SMEM = STAGE + 16;                      // one buffer + one mbarrier (padded)
 };
 
-// FIXUP = false: the pass, with FP32 weights; every tile writes redo[tile] = 1 if a Gauss point
-// of one of its cells left the FP32 range of the weights, else 0, and a tile so marked writes
-// cells[tile * TILE / 8 ...], one bit per cell, which of its cells did.  FIXUP = true: run right
-// after, it redoes those cells with the weights in FP64 (a separate instance keeps that code, and
-// its call, out of the pass's register allocation); the decision per cell keeps every cell's
-// result independent of which cells share its tile.  redo is 4-byte aligned and readable up to
-// the next multiple of 4 bytes past the last tile.
-constexpr int kFixupChunk = 128;  // tiles a warp scans with one 4-byte load per lane
+// FIXUP = false: the pass, with FP32 weights; every tile writes its marks (write_marks) for the
+// cells at which a Gauss point left the FP32 range of the weights.  FIXUP = true: run right after
+// on the marked tiles (MarkScan), it redoes those cells with the weights in FP64 (a separate
+// instance keeps that code, and its call, out of the pass's register allocation); the decision
+// per cell keeps every cell's result independent of which cells share its tile.
 template <int M, int G, bool WALLS, bool FIXUP>
 __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 / WENO_K1_TILE)
     k_reconstruct_char_tma(const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
@@ -1013,40 +1162,15 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
     if (M % 4) tma_load_2d(smem + L::GPM + L::DGS, &map_g1, (int)(tile * L::TILE * 2), 0, &bar[0]);
     tma_load_2d(smem + L::GPM + L::DGS + L::G1, &map_gop, (int)(tile * L::TILE * 4), 0, &bar[0]);
   };
-  // FIXUP: the block scans chunks blockIdx.x, + gridDim.x, ... of kFixupChunk marks; every warp
-  // reads the same words, so all warps walk the same sequence of marked tiles
-  int64_t chunk = (int64_t)blockIdx.x - gridDim.x;
-  uint32_t lanes = 0u, nib = 0u, mine = 0u;
-  int cur = 0;
-  auto next_marked = [&]() -> int64_t {
-    while (nib == 0u) {
-      while (lanes == 0u) {
-        chunk += gridDim.x;
-        if (chunk * kFixupChunk >= ntiles) return ntiles;
-        const int64_t t0 = chunk * kFixupChunk + 4 * (tid & 31);
-        const uint32_t v = t0 < ntiles ? *reinterpret_cast<const uint32_t*>(redo + t0) : 0u;
-        mine = 0u;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (t0 + j < ntiles && ((v >> (8 * j)) & 0xffu)) mine |= 1u << j;
-        lanes = __ballot_sync(0xffffffffu, mine != 0u);
-      }
-      cur = __ffs(lanes) - 1;
-      lanes &= lanes - 1u;
-      nib = __shfl_sync(0xffffffffu, mine, cur);
-    }
-    const int j = __ffs(nib) - 1;
-    nib &= nib - 1u;
-    return chunk * kFixupChunk + 4 * cur + j;
-  };
-  int64_t tile = FIXUP ? next_marked() : (int64_t)blockIdx.x;
+  MarkScan scan(redo, ntiles);
+  int64_t tile = FIXUP ? scan.next() : (int64_t)blockIdx.x;
   if (!FIXUP && tid == 0 && tile < ntiles) issue(tile);
   uint32_t phase = 0u;
   const float4* sgp = reinterpret_cast<const float4*>(smem);
   const float4* sds = reinterpret_cast<const float4*>(smem + L::GPM);
   const float2* sg1 = reinterpret_cast<const float2*>(smem + L::GPM + L::DGS);
   const float4* sgo = reinterpret_cast<const float4*>(smem + L::GPM + L::DGS + L::G1);
-  for (; tile < ntiles; tile = FIXUP ? next_marked() : tile + gridDim.x) {
+  for (; tile < ntiles; tile = FIXUP ? scan.next() : tile + gridDim.x) {
     if (FIXUP && tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the previous tile's reads
       issue(tile);
@@ -1139,20 +1263,9 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
     float amin = 1.0f;
 #pragma unroll 1
     for (int k = 0; k < G / 2; ++k) amin = fminf(amin, face(k, std::integral_constant<bool, FIXUP>{}));
-    if constexpr (!FIXUP) {
-      // weights outside the FP32 range at a cell of the tile (rare): the fix-up pass redoes the
-      // cell (any of its four lanes; lanes 4c..4c+3 of warp w hold cell 8w + c).  Lanes past the
-      // end read the zero fill of the tables and are left out.
-      const uint32_t v = __ballot_sync(0xffffffffu, act && !(amin >= kAlphaMin));
-      const int need = __syncthreads_or(v != 0u);
-      if (need && (tid & 31) == 0) {
-        uint32_t m8 = 0u;
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) m8 |= ((v >> (4 * c8)) & 0xfu) ? 1u << c8 : 0u;
-        cells[tile * (L::TILE / 8) + (tid >> 5)] = (uint8_t)m8;
-      }
-      if (tid == 0) redo[tile] = (uint8_t)need;
-    }
+    // weights outside the FP32 range at a cell of the tile (rare): the fix-up pass redoes the cell
+    // (any of its four lanes).  Lanes past the end read the zero fill of the tables and are left out.
+    if constexpr (!FIXUP) write_marks<L::TILE>(act && !(amin >= kAlphaMin), tile, redo, cells);
     __syncthreads();  // the buffer is free for the next tile's copy
     if (!FIXUP && tid == 0 && next < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -65,7 +65,7 @@ unsigned grid_of(const Launch& l, int64_t work) {
 }
 
 // TMA reconstruction: TILE x 4 threads per block, one TILE-cell tile per iteration.
-constexpr int kTile = weno::dev::TmaTile<12, 8>::TILE;
+constexpr int kTile = weno::dev::PairTile<12, 8>::TILE;
 unsigned tma_grid(const Launch& l, int64_t cells) {
   const int64_t tiles = (cells + kTile - 1) / kTile;
   const int64_t g = l.grid > 0 ? std::min<int64_t>(l.grid, tiles) : tiles;
@@ -96,10 +96,12 @@ struct weno_solver_s {
   // gam = gamma+ then gamma- rows, gam1 = (gamma+_8, gamma-_8) of triangles.
   void *q_gop = nullptr, *q_dg = nullptr, *q_gam = nullptr, *t_gop = nullptr, *t_dg = nullptr, *t_gam = nullptr;
   void *q_gam1 = nullptr, *t_gam1 = nullptr;
+  void *q_pgam = nullptr, *q_pdg = nullptr, *t_pgam = nullptr, *t_pdg = nullptr;  // point-pair tables (Euler FP32C)
   int64_t q_pitch = 0, t_pitch = 0;  // row pitch (cells) of the packed FP32C tables
   bool tma = false;                   // Euler FP32C: reconstruction with TMA-staged tables
   CUtensorMap q_map_gpm{}, q_map_dgs{}, t_map_gpm{}, t_map_dgs{}, t_map_g1{};
   CUtensorMap q_map_gop{}, t_map_gop{};  // gradient operators
+  CUtensorMap q_map_pgam{}, q_map_pdg{}, t_map_pgam{}, t_map_pdg{};  // point-pair tables
   int* err = nullptr;                 // set by a kernel whose bounded wait timed out
   uint8_t* char_redo = nullptr;       // FP32C characteristic tiles whose weights left the FP32 range
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
@@ -175,8 +177,14 @@ int64_t redo_tiles_part(int64_t n) {
   return ((n + t - 1) / t + 15) / 16 * 16;
 }
 int64_t redo_bytes(const S& s) {
-  if (s.fp64 || s.nv != 4 || !s.prm.characteristic) return 0;
+  if (s.fp64 || s.nv != 4) return 0;
   return redo_part(s.nQ) + redo_part(s.nT);
+}
+// Grid of a fix-up pass over n cells: a block per kFixupChunk tiles of marks, at most 4 per SM.
+unsigned fix_grid(const S& s, int64_t n) {
+  constexpr int64_t t = weno::dev::CharTile<12, 8>::TILE;
+  const int64_t chunks = ((n + t - 1) / t + weno::dev::kFixupChunk - 1) / weno::dev::kFixupChunk;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, 4 * s.nsm));
 }
 
 // Cell reconstruction into the Gauss-value array wg.  which: bit 0 = quad group,
@@ -197,15 +205,11 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
         uint8_t* cells_q = redo + redo_tiles_part(s.nQ);
         uint8_t* redo_t = redo + redo_part(s.nQ);
         uint8_t* cells_t = redo_t + redo_tiles_part(s.nT);
-        auto fix_grid = [&](int64_t n) {
-          const int64_t chunks = ((n + CQ::TILE - 1) / CQ::TILE + weno::dev::kFixupChunk - 1) / weno::dev::kFixupChunk;
-          return (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, 4 * s.nsm));
-        };
         if (s.nQ && (which & 1)) {
           weno::dev::k_reconstruct_char_tma<12, 8, WALLS, false><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
               s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
               (float*)wg, eps, gg, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
-          weno::dev::k_reconstruct_char_tma<12, 8, WALLS, true><<<fix_grid(s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
+          weno::dev::k_reconstruct_char_tma<12, 8, WALLS, true><<<fix_grid(s, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
               s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
               (float*)wg, eps, gg, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
         }
@@ -213,7 +217,7 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
           weno::dev::k_reconstruct_char_tma<9, 6, WALLS, false><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
               s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
               8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
-          weno::dev::k_reconstruct_char_tma<9, 6, WALLS, true><<<fix_grid(s.nT), CT::THREADS, CT::SMEM, st>>>(
+          weno::dev::k_reconstruct_char_tma<9, 6, WALLS, true><<<fix_grid(s, s.nT), CT::THREADS, CT::SMEM, st>>>(
               s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
               8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
         }
@@ -231,17 +235,28 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
     }
   }
   if constexpr (COMP && NV == 4) {
-    if (s.tma) {
-      using TQ = weno::dev::TmaTile<12, 8>;
-      using TT = weno::dev::TmaTile<9, 6>;
-      if (s.nQ && (which & 1))
-        weno::dev::k_reconstruct_tma<12, 8, WALLS><<<tma_grid(s.k1q, s.nQ), TQ::THREADS, TQ::SMEM, st>>>(
-            s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, u, ul, s.q_slot, (const float4*)s.q_gop, (const float*)s.area,
-            s.nQ, s.q_pitch, 0, 0, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
-      if (s.nT && (which & 2))
-        weno::dev::k_reconstruct_tma<9, 6, WALLS><<<tma_grid(s.k1t, s.nT), TT::THREADS, TT::SMEM, st>>>(
-            s.t_map_gpm, s.t_map_dgs, s.t_map_g1, u, ul, s.t_slot, (const float4*)s.t_gop, (const float*)s.area,
-            s.nT, s.t_pitch, s.nQ, 8 * s.nQ, (float*)wg, eps, s.prm.linear, s.err, s.debug_stall);
+    if (s.tma) {  // each pass is followed by its fix-up pass over the cells it marked
+      using PQ = weno::dev::PairTile<12, 8>;
+      using PT = weno::dev::PairTile<9, 6>;
+      uint8_t* cells_q = redo + redo_tiles_part(s.nQ);
+      uint8_t* redo_t = redo + redo_part(s.nQ);
+      uint8_t* cells_t = redo_t + redo_tiles_part(s.nT);
+      if (s.nQ && (which & 1)) {
+        weno::dev::k_reconstruct_tma<12, 8, WALLS, false><<<tma_grid(s.k1q, s.nQ), PQ::THREADS, PQ::SMEM, st>>>(
+            s.q_map_pgam, s.q_map_pdg, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0, (float*)wg,
+            eps, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
+        weno::dev::k_reconstruct_tma<12, 8, WALLS, true><<<fix_grid(s, s.nQ), PQ::THREADS, PQ::SMEM, st>>>(
+            s.q_map_pgam, s.q_map_pdg, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0, (float*)wg,
+            eps, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
+      }
+      if (s.nT && (which & 2)) {
+        weno::dev::k_reconstruct_tma<9, 6, WALLS, false><<<tma_grid(s.k1t, s.nT), PT::THREADS, PT::SMEM, st>>>(
+            s.t_map_pgam, s.t_map_pdg, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ, 8 * s.nQ,
+            (float*)wg, eps, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
+        weno::dev::k_reconstruct_tma<9, 6, WALLS, true><<<fix_grid(s, s.nT), PT::THREADS, PT::SMEM, st>>>(
+            s.t_map_pgam, s.t_map_pdg, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ, 8 * s.nQ,
+            (float*)wg, eps, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
+      }
       return;
     }
   }
@@ -427,9 +442,9 @@ int upload_real(S& s, void** dst, const std::vector<double>& src, cudaStream_t s
 //   gam1 [g][q]       float2 (gamma+_8, gamma-_8) of triangles
 // The splitting of Section 3.4 depends on the geometry only; it is evaluated
 // here in FP64: gt+ = (gamma + theta|gamma|)/2, gt- = gt+ - gamma,
-// sigma+- = sum gt+-, gamma+- = gt+- / sigma+-.
+// sigma+- = sum gt+-, gamma+- = gt+- / sigma+-.  rows = false uploads gop only.
 int upload_packed(S& s, const GroupTables& T, int64_t P, double theta, void** gop, void** dg, void** gam,
-                  void** gam1, cudaStream_t st) {
+                  void** gam1, cudaStream_t st, bool rows = true) {
   const int64_t N = T.N;
   const int M = T.M, G = T.G, M4 = M / 4;
   std::vector<float> a((size_t)M * 4 * P, 0.f), b((size_t)G * 4 * P, 0.f), c((size_t)G * 2 * M4 * 4 * P, 0.f), e;
@@ -463,17 +478,62 @@ int upload_packed(S& s, const GroupTables& T, int64_t P, double theta, void** go
       }
     }
   }
-  float *pa, *pb, *pc, *pe = nullptr;
+  float *pa, *pb = nullptr, *pc = nullptr, *pe = nullptr;
   int r;
   if ((r = upload(s, &pa, a, st))) return r;
-  if ((r = upload(s, &pb, b, st))) return r;
-  if ((r = upload(s, &pc, c, st))) return r;
-  if (M % 4 && (r = upload(s, &pe, e, st))) return r;
+  if (rows && (r = upload(s, &pb, b, st))) return r;
+  if (rows && (r = upload(s, &pc, c, st))) return r;
+  if (rows && M % 4 && (r = upload(s, &pe, e, st))) return r;
   CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
   *gop = pa;
   *dg = pb;
   *gam = pc;
   *gam1 = pe;
+  return WENO_OK;
+}
+
+// Point-pair tables of the Euler FP32C reconstruction (k_reconstruct_tma), rows of P >= N cells
+// of float4, the G Gauss points of a cell taken as G/2 pairs (points 2k, 2k+1 of face k):
+//   gam [k][j][q]   (gamma+_j(2k), gamma+_j(2k+1), gamma-_j(2k), gamma-_j(2k+1))
+//   dg  [2k][q]     (dx(2k), dx(2k+1), dy(2k), dy(2k+1)), (dx, dy) = x_G - c0
+//   dg  [2k+1][q]   (sigma+(2k), sigma+(2k+1), sigma-(2k), sigma-(2k+1))
+// with the splitting of Section 3.4 evaluated in FP64 as in upload_packed.
+int upload_pairs(S& s, const GroupTables& T, int64_t P, double theta, void** gam, void** dg, cudaStream_t st) {
+  const int64_t N = T.N;
+  const int M = T.M, G = T.G;
+  std::vector<float> a((size_t)(G / 2) * M * 4 * P, 0.f), b((size_t)G * 4 * P, 0.f);
+  std::vector<double> gp(M), gn(M);
+  for (int g = 0; g < G; ++g) {
+    const int k = g / 2, h = g % 2;
+    for (int64_t q = 0; q < N; ++q) {
+      double sp = 0.0, sm = 0.0;
+      for (int j = 0; j < M; ++j) {
+        const double x = T.gam[((size_t)g * M + j) * N + q];
+        gp[j] = 0.5 * (x + theta * std::fabs(x));
+        gn[j] = gp[j] - x;
+        sp += gp[j];
+        sm += gn[j];
+      }
+      for (int j = 0; j < M; ++j) {
+        float* r = &a[(((size_t)k * M + j) * P + q) * 4];
+        r[h] = (float)(gp[j] / sp);
+        r[2 + h] = (float)(gn[j] / sm);
+      }
+      float* d0 = &b[((size_t)(2 * k) * P + q) * 4];
+      float* d1 = &b[((size_t)(2 * k + 1) * P + q) * 4];
+      d0[h] = (float)T.dg[((size_t)g * 2 + 0) * N + q];
+      d0[2 + h] = (float)T.dg[((size_t)g * 2 + 1) * N + q];
+      d1[h] = (float)sp;
+      d1[2 + h] = (float)sm;
+    }
+  }
+  float *pa, *pb;
+  int r;
+  if ((r = upload(s, &pa, a, st))) return r;
+  if ((r = upload(s, &pb, b, st))) return r;
+  CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  *gam = pa;
+  *dg = pb;
   return WENO_OK;
 }
 
@@ -503,27 +563,37 @@ int setup_tma(S& s) {
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
   if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return fail(WENO_ECUDA, "cuTensorMapEncodeTiled unavailable");
   EncodeTiled enc = reinterpret_cast<EncodeTiled>(fn);
-  using TQ = weno::dev::TmaTile<12, 8>;
-  using TT = weno::dev::TmaTile<9, 6>;
+  using PQ = weno::dev::PairTile<12, 8>;
+  using PT = weno::dev::PairTile<9, 6>;
   int r;
-  // rows: gamma+-: G * 2 * (M/4) float4 rows; (x_G - c0, sigma+-): G float4 rows; triangle extras: G float2 rows
+  // point-pair tables: gamma+- (G/2) * M float4 rows, offsets and sigma+- G float4 rows
   if (s.nQ) {
+    if ((r = make_map_2d(enc, &s.q_map_pgam, s.q_pgam, 4 * s.q_pitch, 4 * 12, 16 * s.q_pitch, 4 * kTile, 4 * 12)))
+      return r;
+    if ((r = make_map_2d(enc, &s.q_map_pdg, s.q_pdg, 4 * s.q_pitch, 8, 16 * s.q_pitch, 4 * kTile, 8))) return r;
+  }
+  if (s.nT) {
+    if ((r = make_map_2d(enc, &s.t_map_pgam, s.t_pgam, 4 * s.t_pitch, 3 * 9, 16 * s.t_pitch, 4 * kTile, 3 * 9)))
+      return r;
+    if ((r = make_map_2d(enc, &s.t_map_pdg, s.t_pdg, 4 * s.t_pitch, 6, 16 * s.t_pitch, 4 * kTile, 6))) return r;
+  }
+  for (auto fn : {weno::dev::k_reconstruct_tma<12, 8, false, false>, weno::dev::k_reconstruct_tma<12, 8, true, false>,
+                  weno::dev::k_reconstruct_tma<12, 8, false, true>, weno::dev::k_reconstruct_tma<12, 8, true, true>})
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PQ::SMEM));
+  for (auto fn : {weno::dev::k_reconstruct_tma<9, 6, false, false>, weno::dev::k_reconstruct_tma<9, 6, true, false>,
+                  weno::dev::k_reconstruct_tma<9, 6, false, true>, weno::dev::k_reconstruct_tma<9, 6, true, true>})
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM));
+  // the characteristic kernel's rows: gamma+-: G * 2 * (M/4) float4 rows; (x_G - c0, sigma+-): G
+  // float4 rows; triangle extras: G float2 rows
+  if (s.prm.characteristic && s.nQ) {
     if ((r = make_map_2d(enc, &s.q_map_gpm, s.q_gam, 4 * s.q_pitch, 8 * 6, 16 * s.q_pitch, 4 * kTile, 8 * 6))) return r;
     if ((r = make_map_2d(enc, &s.q_map_dgs, s.q_dg, 4 * s.q_pitch, 8, 16 * s.q_pitch, 4 * kTile, 8))) return r;
   }
-  if (s.nT) {
+  if (s.prm.characteristic && s.nT) {
     if ((r = make_map_2d(enc, &s.t_map_gpm, s.t_gam, 4 * s.t_pitch, 6 * 4, 16 * s.t_pitch, 4 * kTile, 6 * 4))) return r;
     if ((r = make_map_2d(enc, &s.t_map_dgs, s.t_dg, 4 * s.t_pitch, 6, 16 * s.t_pitch, 4 * kTile, 6))) return r;
     if ((r = make_map_2d(enc, &s.t_map_g1, s.t_gam1, 2 * s.t_pitch, 6, 8 * s.t_pitch, 2 * kTile, 6))) return r;
   }
-  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          TQ::SMEM));
-  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          TT::SMEM));
-  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<12, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          TQ::SMEM));
-  CK(cudaFuncSetAttribute(weno::dev::k_reconstruct_tma<9, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          TT::SMEM));
   // D_j^+ rows: M float4 rows
   if (s.nQ && (r = make_map_2d(enc, &s.q_map_gop, s.q_gop, 4 * s.q_pitch, 12, 16 * s.q_pitch, 4 * kTile, 12)))
     return r;
@@ -783,8 +853,15 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   } else {
     d.q_pitch = (d.nQ + 63) / 64 * 64;
     d.t_pitch = (d.nT + 63) / 64 * 64;
-    if ((r = upload_packed(d, tq, d.q_pitch, p.theta, &d.q_gop, &d.q_dg, &d.q_gam, &d.q_gam1, st))) return r;
-    if ((r = upload_packed(d, tt, d.t_pitch, p.theta, &d.t_gop, &d.t_dg, &d.t_gam, &d.t_gam1, st))) return r;
+    // the split-weight rows of upload_packed serve the scalar and the characteristic kernels; the
+    // component-wise Euler kernel reads the point-pair tables
+    const bool rows = d.nv != 4 || p.characteristic;
+    if ((r = upload_packed(d, tq, d.q_pitch, p.theta, &d.q_gop, &d.q_dg, &d.q_gam, &d.q_gam1, st, rows))) return r;
+    if ((r = upload_packed(d, tt, d.t_pitch, p.theta, &d.t_gop, &d.t_dg, &d.t_gam, &d.t_gam1, st, rows))) return r;
+    if (d.nv == 4) {
+      if ((r = upload_pairs(d, tq, d.q_pitch, p.theta, &d.q_pgam, &d.q_pdg, st))) return r;
+      if ((r = upload_pairs(d, tt, d.t_pitch, p.theta, &d.t_pgam, &d.t_pdg, st))) return r;
+    }
   }
   {
     std::vector<double> inv(d.N);
@@ -1080,7 +1157,7 @@ int weno_autotune(weno_solver_t s, const void* U, const void* U_lo, void* cuda_s
   for (int b : blocks)
     for (int w : waves) generic.push_back(Launch{b, w == 0 ? 0 : w * s->nsm * std::max(1, 2048 / b)});
   // TMA reconstruction: TILE x 4 threads; 1-4 blocks of 256 threads per SM (persistent), or one block per tile
-  for (int w : {0, 1, 2, 3, 4}) tma.push_back(Launch{weno::dev::TmaTile<12, 8>::THREADS, w * s->nsm * (64 / kTile)});
+  for (int w : {0, 1, 2, 3, 4}) tma.push_back(Launch{weno::dev::PairTile<12, 8>::THREADS, w * s->nsm * (64 / kTile)});
   auto tune = [&](Launch& L, auto run, const std::vector<Launch>& cands) -> int {
     float best = 1e30f;
     Launch bestL = L;
