@@ -385,14 +385,22 @@ def k1_bytes(nQ, nT, nv, esz, comp):
 def k1_ops(nQ, nT, nv=4):
     """Algorithmic FP32 operations (an FMA counts one) of one reconstruction pass (Sections 3.1-3.4).
 
-    Per (cell, variable): 3 per stencil slot (Delta W from hi and lo) and 8 per candidate
-    (gradient 4, beta 3, beta + eps 1); per Gauss point and candidate 16 (P^1_j(x_G) - W0: 2;
-    per sign: q = gamma beta, q + q^2, beta (1 + q + q^2) + eps, its square, alpha = gamma r,
-    sum alpha, sum alpha p: 7); per Gauss point 10 for R = W0 + sigma+ B+/A+ - sigma- B-/A-.
-    Reciprocals (2 per Gauss point and candidate, 2 per Gauss point) run on the MUFU pipe and are
-    not counted."""
+    Per (cell, variable): 3 per stencil slot (Delta W from hi and lo) and 10 per candidate
+    (gradient 4, beta 3, beta + eps, beta^2, beta^3); per Gauss point and candidate 14
+    (P^1_j(x_G) - W0: 2; per sign: beta~ + eps = (beta + eps) + gamma (beta^2 + gamma beta^3) 2,
+    its square, alpha = gamma r, sum alpha, sum alpha p: 6); per Gauss point 10 for
+    R = W0 + sigma+ B+/A+ - sigma- B-/A-.  Reciprocals (k1_rcp) run on the MUFU pipe and are not
+    counted."""
     def per(M, G):
-        return nv * (11 * M + G * (16 * M + 10))
+        return nv * (13 * M + G * (14 * M + 10))
+    return nQ * per(12, 8) + nT * per(9, 6)
+
+
+def k1_rcp(nQ, nT, nv=4):
+    """Reciprocals (MUFU) of one reconstruction pass: 2 per Gauss point and candidate (one per sign)
+    and 2 per Gauss point (1 / sum alpha+-), per (cell, variable)."""
+    def per(M, G):
+        return nv * G * (2 * M + 2)
     return nQ * per(12, 8) + nT * per(9, 6)
 
 
@@ -961,6 +969,7 @@ def main():
     kbytes = k1_bytes(nQ, nT, 4, 4, True)
     achieved = kbytes / (k_ms / 1e3) / 1e9
     kops = k1_ops(nQ, nT)
+    krcp = k1_rcp(nQ, nT)
     alu_peak = peaks["fp32_fma"]
     alu_achieved = kops / (k_ms / 1e3) / 1e12
     traffic = k1_traffic(nQ, nT)
@@ -1085,8 +1094,9 @@ def main():
                                                     for n in (20, 40, 80, args.acc_n)], precs),
                   "vortex_lowq": ladder_orders([ladder_point("vortex-lowq", n, precs) for n in (40, 80, 160)], precs)}
 
-    # k_fill of dt, the three stages, k_advance_time
-    launches_per_step = 2 + 3 * ((1 if nQ else 0) + (1 if nT else 0) + 1 + (1 if nQ else 0) + (1 if nT else 0))
+    # k_fill of dt, the three stages (per cell type the reconstruction, its fix-up pass and the
+    # gather; the face kernel), k_advance_time
+    launches_per_step = 2 + 3 * (3 * (1 if nQ else 0) + 3 * (1 if nT else 0) + 1)
     launch_cfg = sol.launch_config().tolist()
     del sol64, V
     batched = None
@@ -1109,12 +1119,16 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "steps": e2e_steps},
             # the reconstruction is bound by its arithmetic (the FMA pipe and the reciprocals' MUFU pipe,
-            # each about half of its time), not by HBM; the HBM views follow
+            # each busy for more than half of its time), not by HBM; the HBM views follow
             "roofline": {"kernel": "k_reconstruct_tma (quad + triangle launches of one pass)", "bound": "alu",
                          "achieved": alu_achieved, "peak": alu_peak, "unit": "Top/s (FP32 ops, FMA = 1)",
                          "frac": alu_achieved / alu_peak,
                          "peak_source": "measured FP32 FMA throughput of this GPU (weno_probe_peak)",
-                         "traffic": traffic, "algorithmic_ops_per_launch": kops, "ms_per_launch": k_ms},
+                         "traffic": traffic, "algorithmic_ops_per_launch": kops, "ms_per_launch": k_ms,
+                         # the reciprocals' pipe, measured the same way
+                         "mufu": {"achieved": krcp / (k_ms / 1e3) / 1e12, "peak": peaks["rcp"],
+                                  "unit": "T reciprocals/s", "frac": krcp / (k_ms / 1e3) / 1e12 / peaks["rcp"],
+                                  "reciprocals_per_launch": krcp}},
             "peaks_measured": {"unit": "Top/s (FMA = 1)", **peaks},
             "roofline_step_hbm": {"bound": "hbm", "achieved": step_achieved, "peak": peak, "unit": "GB/s",
                                   "frac": step_achieved / peak, "algorithmic_bytes_per_stage": sbytes,

@@ -593,8 +593,10 @@ constexpr float kBetaMax = 1e12f;
 //   R - W0 = sigma+ sum alpha+ p / sum alpha+  -  sigma- sum alpha- p / sum alpha-
 // (the linear scheme: sigma+ sum gamma+ p - sigma- sum gamma- p).  Candidates are the outer loop,
 // and the two points of a face share the paired FP32 instructions, so the per-point sums are the
-// only state kept across candidates.  Returns false if a sum of alpha fell below kAlphaMin (or is
-// not a number): the caller then has the cell redone with FP64 weights.
+// only state kept across candidates.  Returns false if a sum of alpha fell below kAlphaMin: the
+// caller then has the cell redone with FP64 weights.  From finite inputs the sums are finite (the
+// clamp below keeps beta^3 finite, and an overflowing square gives alpha = 0); a NaN sum comes from
+// a NaN state, which FP64 weights cannot mend, and is left to the caller's state check.
 template <int M, int G>
 __device__ __forceinline__ bool pair_points(const float4* __restrict__ sgam, const float4* __restrict__ sdg,
                                             const float4* __restrict__ sgo, int cl, const float* dW, float a0,
@@ -637,7 +639,8 @@ __device__ __forceinline__ bool pair_points(const float4* __restrict__ sgam, con
     const float4 m = sgo[j * TILE + cl];
     const float da = dW[Sub<M>::a(j)], db = dW[Sub<M>::b(j)];
     const float gx = fmaf(m.x, da, m.y * db), gy = fmaf(m.z, da, m.w * db);
-    const float b = fminf(a0 * fmaf(gx, gx, gy * gy), kBetaMax);
+    const float b0 = a0 * fmaf(gx, gx, gy * gy);
+    const float b = b0 > kBetaMax ? kBetaMax : b0;  // keeps a NaN (fminf would drop it)
     const float b2 = b * b, b3 = b2 * b, be = b + eps;
     const float2 GX = f2(gx, gx), GY = f2(gy, gy), C0 = f2(be, be), C1 = f2(b2, b2), C2 = f2(b3, b3);
 #pragma unroll
@@ -661,7 +664,7 @@ __device__ __forceinline__ bool pair_points(const float4* __restrict__ sgam, con
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const float4 s = sdg[(2 * k + 1) * TILE + cl];
-    ok = ok && Ap[k].x >= kAlphaMin && Ap[k].y >= kAlphaMin && Am[k].x >= kAlphaMin && Am[k].y >= kAlphaMin;
+    ok = ok && !(Ap[k].x < kAlphaMin) && !(Ap[k].y < kAlphaMin) && !(Am[k].x < kAlphaMin) && !(Am[k].y < kAlphaMin);
     const float i0 = s.x * Bp[k].x * rcp_approx(Ap[k].x) - s.z * Bm[k].x * rcp_approx(Am[k].x);
     const float i1 = s.y * Bp[k].y * rcp_approx(Ap[k].y) - s.w * Bm[k].y * rcp_approx(Am[k].y);
     out[(2 * k) * 4] = w0 + (l0 + i0);
