@@ -30,11 +30,12 @@ METRIC = "WENO3 cell-updates/s (×RK stages) on 1 GB300, FP32+batched vs FP64 at
 UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per cell of one reconstruction launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of
-# k_reconstruct_tma (the pass and its FP64 fix-up launch) on the 637k-cell mesh of the benchmark
-# family (n = 700), divided by its cells of each type.  They describe the kernel source they were
-# captured on (SHA-256 of csrc/kernels.cuh); for any other source the bench line reports traffic null.
-K1_TRAFFIC = {"kernels_cuh_sha256": "1b9ff18829a726bafa8340882ef85d6239346b7abe98a9322aeae5252707c8d2",
-              "quad": 1305.2, "tri": 852.0}
+# k_reconstruct_tma and of k_reconstruct_char_tma (each pass with its FP64 fix-up launch) on the
+# 637k-cell mesh of the benchmark family (n = 700), divided by its cells of each type.  They describe
+# the kernel source they were captured on (SHA-256 of csrc/kernels.cuh); for any other source the
+# bench line reports traffic null.
+K1_TRAFFIC = {"kernels_cuh_sha256": "5b667bd92fe3de3efdeffa43428cf0a413db9e55103b26e2c10e98df825471e7",
+              "quad": 1304.7, "tri": 847.5, "char_quad": 1308.3, "char_tri": 857.1}
 WORKLOAD_N = 1754
 
 
@@ -344,14 +345,15 @@ def run_batched(args, torch, stream, dist=None, ws=1):
             "nonphysical_riemann_instances": int(sum(1 for d, b in zip(descs, bad) if b and d["data"] == "riemann"))}
 
 
-def k1_traffic(nQ, nT):
-    """ncu DRAM bytes of one reconstruction pass, or None if the kernel source changed since the capture."""
+def k1_traffic(nQ, nT, kind=""):
+    """ncu DRAM bytes of one reconstruction pass (kind "" component-wise, "char_" characteristic), or
+    None if the kernel source changed since the capture."""
     import hashlib
     src = os.path.join(ROOT, "paper_1712_08317_gb300", "csrc", "kernels.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if K1_TRAFFIC["kernels_cuh_sha256"] != sha or K1_TRAFFIC["quad"] is None:
+    if K1_TRAFFIC["kernels_cuh_sha256"] != sha or K1_TRAFFIC[kind + "quad"] is None:
         return None
-    return nQ * K1_TRAFFIC["quad"] + nT * K1_TRAFFIC["tri"]
+    return nQ * K1_TRAFFIC[kind + "quad"] + nT * K1_TRAFFIC[kind + "tri"]
 
 
 def measure_peaks():
@@ -419,10 +421,10 @@ def k1_ops_char(nQ, nT):
     """Algorithmic FP32 operations (FMA = 1) of one characteristic-variable reconstruction pass:
     per (cell, field) 3 per stencil slot (Delta W); per face the Roe frame (60), the projection of
     the slot differences onto the field (4 per slot) and the field's candidate gradients and
-    indicators (8 per candidate); per Gauss point the weights (16 per candidate + 10) and the
-    back-projection (4)."""
+    indicators (10 per candidate, as in k1_ops); per Gauss point the weights (14 per candidate + 10,
+    as in k1_ops) and the back-projection (4)."""
     def per(M, G):
-        return 4 * (3 * M + (G // 2) * (60 + 4 * M + 8 * M) + G * (16 * M + 14))
+        return 4 * (3 * M + (G // 2) * (60 + 4 * M + 10 * M) + G * (14 * M + 14))
     return nQ * per(12, 8) + nT * per(9, 6)
 
 
@@ -1078,6 +1080,7 @@ def main():
                              "bound": "alu", "achieved": char_ops / (char_k1 / 1e3) / 1e12, "peak": alu_peak,
                              "unit": "Top/s (FP32 ops, FMA = 1)",
                              "frac": char_ops / (char_k1 / 1e3) / 1e12 / alu_peak,
+                             "traffic": k1_traffic(nQ, nT, "char_"),
                              "algorithmic_ops_per_launch": char_ops, "ms_per_launch": char_k1}}
         del solc, Uc, Ulc
         torch.cuda.empty_cache()

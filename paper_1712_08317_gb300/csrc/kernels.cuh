@@ -506,6 +506,9 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 #ifndef WENO_K1_TILE
 #define WENO_K1_TILE 16  // cells per block tile of the TMA reconstruction (8, 16, 32 or 64)
 #endif
+#ifndef WENO_K1_DG_LDS
+#define WENO_K1_DG_LDS 0  // 1: the TMA reconstruction re-reads the Gauss offsets from shared memory
+#endif
 static_assert(WENO_K1_TILE == 8 || WENO_K1_TILE == 16 || WENO_K1_TILE == 32 || WENO_K1_TILE == 64, "tile of 8, 16, 32 or 64 cells");
 
 constexpr int kFixupChunk = 128;  // tiles a warp of a fix-up pass scans with one 4-byte load per lane
@@ -602,12 +605,24 @@ __device__ __forceinline__ bool pair_points(const float4* __restrict__ sgam, con
                                             const float4* __restrict__ sgo, int cl, const float* dW, float a0,
                                             float eps, int linear, float w0, float l0, float* __restrict__ out) {
   constexpr int NP = G / 2, TILE = WENO_K1_TILE;
-  float2 dx[NP], dy[NP], Ap[NP], Bp[NP], Am[NP], Bm[NP];
+  float2 Ap[NP], Bp[NP], Am[NP], Bm[NP];
+#if WENO_K1_DG_LDS
+  // the offsets of face k's points, read from shared memory where they are used (fewer registers)
+  auto DX = [&](int k) { const float4 r = sdg[(2 * k) * TILE + cl]; return f2(r.x, r.y); };
+  auto DY = [&](int k) { const float4 r = sdg[(2 * k) * TILE + cl]; return f2(r.z, r.w); };
+#else
+  float2 dx[NP], dy[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const float4 r = sdg[(2 * k) * TILE + cl];
     dx[k] = f2(r.x, r.y);
     dy[k] = f2(r.z, r.w);
+  }
+  auto DX = [&](int k) { return dx[k]; };
+  auto DY = [&](int k) { return dy[k]; };
+#endif
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
     Ap[k] = f2(0.f, 0.f); Bp[k] = f2(0.f, 0.f);
     Am[k] = f2(0.f, 0.f); Bm[k] = f2(0.f, 0.f);
   }
@@ -621,7 +636,7 @@ __device__ __forceinline__ bool pair_points(const float4* __restrict__ sgam, con
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
         const float4 g4 = sgam[(k * M + j) * TILE + cl];
-        const float2 p = __ffma2_rn(GX, dx[k], __fmul2_rn(GY, dy[k]));
+        const float2 p = __ffma2_rn(GX, DX(k), __fmul2_rn(GY, DY(k)));
         Bp[k] = __ffma2_rn(f2(g4.x, g4.y), p, Bp[k]);
         Bm[k] = __ffma2_rn(f2(g4.z, g4.w), p, Bm[k]);
       }
@@ -647,7 +662,7 @@ __device__ __forceinline__ bool pair_points(const float4* __restrict__ sgam, con
     for (int k = 0; k < NP; ++k) {
       const float4 g4 = sgam[(k * M + j) * TILE + cl];
       const float2 gp = f2(g4.x, g4.y), gn = f2(g4.z, g4.w);
-      const float2 p = __ffma2_rn(GX, dx[k], __fmul2_rn(GY, dy[k]));
+      const float2 p = __ffma2_rn(GX, DX(k), __fmul2_rn(GY, DY(k)));
       const float2 dp = __ffma2_rn(gp, __ffma2_rn(gp, C2, C1), C0);  // beta~+ + eps at both points
       const float2 dn = __ffma2_rn(gn, __ffma2_rn(gn, C2, C1), C0);
       const float2 ap = __fmul2_rn(gp, rcp2(__fmul2_rn(dp, dp)));
@@ -713,8 +728,19 @@ __device__ __forceinline__ void pair_points_fp64(const float4* __restrict__ sgam
 // (write_marks) for the cells whose sums of alpha left the FP32 range.  FIXUP = true: run right
 // after on the marked tiles only (MarkScan), it redoes the marked cells with FP64 weights; the
 // decision per cell keeps every cell's result independent of which cells share its tile.
+#ifndef WENO_K1_BLOCKS_Q
+#define WENO_K1_BLOCKS_Q (WENO_K1_MIN_BLOCKS * 64 / WENO_K1_TILE)  // resident blocks per SM, quads
+#endif
+#ifndef WENO_K1_BLOCKS_T
+// triangles: 80 registers without spills, 24 warps per SM (measured 2.6 % faster per pass than at
+// the quads' 16 warps, whose 122 registers spill when cut to 96)
+#define WENO_K1_BLOCKS_T (WENO_K1_MIN_BLOCKS * 96 / WENO_K1_TILE)  // resident blocks per SM, triangles
+#endif
+// The register budget of k_reconstruct_tma<M, ...>: 65,536 / (blocks x TILE x 4) per thread.
+template <int M> struct K1Blocks { static constexpr int value = M == 12 ? WENO_K1_BLOCKS_Q : WENO_K1_BLOCKS_T; };
+
 template <int M, int G, bool WALLS, bool FIXUP>
-__global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_K1_MIN_BLOCKS * 64 / WENO_K1_TILE) k_reconstruct_tma(
+__global__ void __launch_bounds__(WENO_K1_TILE * 4, K1Blocks<M>::value) k_reconstruct_tma(
     const __grid_constant__ CUtensorMap map_gam, const __grid_constant__ CUtensorMap map_dg,
     const __grid_constant__ CUtensorMap map_gop, const float* __restrict__ U, const float* __restrict__ Ulo,
     const int32_t* __restrict__ slot, const float* __restrict__ area, int64_t N, int64_t first, int64_t gbase,
@@ -1113,41 +1139,116 @@ __global__ void __launch_bounds__(256) k_reconstruct_char(
 #define WENO_KCHAR_MIN_BLOCKS 2  // resident 256-thread blocks per SM the characteristic kernel's registers allow
 #endif
 
-// FP32C characteristic reconstruction with the tile's tables (split weights,
-// Gauss offsets and sigma+-, gradient operators) staged in shared memory by TMA,
-// as in k_reconstruct_tma: the per-face re-reads of the gradient operators and
-// the per-point weights come from shared memory.  Lanes of cells past the end
-// compute on the last cell's data and store nothing.
-template <int M, int G>
-struct CharTile {
-  static constexpr int TILE = WENO_K1_TILE;
-  static constexpr int THREADS = TILE * 4;
-  static constexpr int M4 = M / 4;
-  static constexpr int GPM = G * 2 * M4 * TILE * 16;
-  static constexpr int DGS = G * TILE * 16;
-  static constexpr int G1 = (M % 4) ? G * TILE * 8 : 0;
-  static constexpr int GOP = M * TILE * 16;                    // D_j^+ rows
-  static constexpr int STAGE = GPM + DGS + G1 + GOP;           // bytes, multiple of 128
-  static constexpr int SMEM = STAGE + 16;                      // one buffer + one mbarrier (padded)
-};
+// Increments R(x_G) - W0 of one field at the two Gauss points of face k from that field's stencil
+// differences dU (dU[0] = 0) and the tile's point-pair tables (PairTile rows), FP32: the arithmetic
+// of pair_points for a single face, candidates outer, both points in one paired instruction.
+// Returns false if a sum of alpha fell below kAlphaMin (the cell then goes to the FP64 fix-up).
+template <int M>
+__device__ __forceinline__ bool face_pair(const float4* __restrict__ sgam, const float4* __restrict__ sdg,
+                                          const float4* __restrict__ sgo, int cl, int k, const float* dU, float a0,
+                                          float eps, int linear, float2& incr) {
+  constexpr int TILE = WENO_K1_TILE;
+  const float4 r = sdg[(2 * k) * TILE + cl], s = sdg[(2 * k + 1) * TILE + cl];
+  const float2 dx = f2(r.x, r.y), dy = f2(r.z, r.w);
+  float2 Ap = f2(0.f, 0.f), Bp = f2(0.f, 0.f), Am = f2(0.f, 0.f), Bm = f2(0.f, 0.f);
+  if (linear) {
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float4 m = sgo[j * TILE + cl];
+      const float da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
+      const float gx = fmaf(m.x, da, m.y * db), gy = fmaf(m.z, da, m.w * db);
+      const float4 g4 = sgam[(k * M + j) * TILE + cl];
+      const float2 p = __ffma2_rn(f2(gx, gx), dx, __fmul2_rn(f2(gy, gy), dy));
+      Bp = __ffma2_rn(f2(g4.x, g4.y), p, Bp);
+      Bm = __ffma2_rn(f2(g4.z, g4.w), p, Bm);
+    }
+    incr = f2(s.x * Bp.x - s.z * Bm.x, s.y * Bp.y - s.w * Bm.y);
+    return true;
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float4 m = sgo[j * TILE + cl];
+    const float da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
+    const float gx = fmaf(m.x, da, m.y * db), gy = fmaf(m.z, da, m.w * db);
+    const float b0 = a0 * fmaf(gx, gx, gy * gy);
+    const float b = b0 > kBetaMax ? kBetaMax : b0;  // keeps a NaN
+    const float b2 = b * b, b3 = b2 * b, be = b + eps;
+    const float2 C0 = f2(be, be), C1 = f2(b2, b2), C2 = f2(b3, b3);
+    const float4 g4 = sgam[(k * M + j) * TILE + cl];
+    const float2 gp = f2(g4.x, g4.y), gn = f2(g4.z, g4.w);
+    const float2 p = __ffma2_rn(f2(gx, gx), dx, __fmul2_rn(f2(gy, gy), dy));
+    const float2 dp = __ffma2_rn(gp, __ffma2_rn(gp, C2, C1), C0);  // beta~+ + eps at both points
+    const float2 dn = __ffma2_rn(gn, __ffma2_rn(gn, C2, C1), C0);
+    const float2 ap = __fmul2_rn(gp, rcp2(__fmul2_rn(dp, dp)));
+    const float2 an = __fmul2_rn(gn, rcp2(__fmul2_rn(dn, dn)));
+    Ap = __fadd2_rn(Ap, ap);
+    Bp = __ffma2_rn(ap, p, Bp);
+    Am = __fadd2_rn(Am, an);
+    Bm = __ffma2_rn(an, p, Bm);
+  }
+  incr = f2(s.x * Bp.x * rcp_approx(Ap.x) - s.z * Bm.x * rcp_approx(Am.x),
+            s.y * Bp.y * rcp_approx(Ap.y) - s.w * Bm.y * rcp_approx(Am.y));
+  return !(Ap.x < kAlphaMin) && !(Ap.y < kAlphaMin) && !(Am.x < kAlphaMin) && !(Am.y < kAlphaMin);
+}
 
+// face_pair with the nonlinear weights in FP64 (IEEE division, indicators unclamped): the fix-up
+// of cells whose FP32 sums of alpha left the range.
+template <int M>
+__device__ __forceinline__ void face_pair_fp64(const float4* __restrict__ sgam, const float4* __restrict__ sdg,
+                                               const float4* __restrict__ sgo, int cl, int k, const float* dU,
+                                               float a0, float eps, float2& incr) {
+  constexpr int TILE = WENO_K1_TILE;
+  const float4 r = sdg[(2 * k) * TILE + cl], s = sdg[(2 * k + 1) * TILE + cl];
+  float out[2];
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const float dxg = h ? r.y : r.x, dyg = h ? r.w : r.z;
+    double Ap = 0.0, Bp = 0.0, Am = 0.0, Bm = 0.0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float4 m = sgo[j * TILE + cl];
+      const float da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
+      const float gx = fmaf(m.x, da, m.y * db), gy = fmaf(m.z, da, m.w * db);
+      const double b = (double)a0 * ((double)gx * gx + (double)gy * gy);
+      const double pj = fmaf(gx, dxg, gy * dyg);
+      const float4 g4 = sgam[(k * M + j) * TILE + cl];
+      const double gp = h ? g4.y : g4.x, gn = h ? g4.w : g4.z;
+      const double qp = gp * b, qn = gn * b;
+      const double dp = b * (1.0 + qp + qp * qp) + eps, dn = b * (1.0 + qn + qn * qn) + eps;
+      const double ap = gp / (dp * dp), an = gn / (dn * dn);
+      Ap += ap;
+      Bp += ap * pj;
+      Am += an;
+      Bm += an * pj;
+    }
+    const double sp = h ? s.y : s.x, sm = h ? s.w : s.z;
+    out[h] = (float)(sp * (Bp / Ap) - sm * (Bm / Am));
+  }
+  incr = f2(out[0], out[1]);
+}
+
+// FP32C characteristic reconstruction with the tile's point-pair tables (split weights, Gauss
+// offsets and sigma+-, gradient operators; the PairTile layout of k_reconstruct_tma) staged in
+// shared memory by TMA.  Per face, each lane builds the Roe frame, projects the stencil
+// differences onto its field and evaluates the face's two Gauss points with face_pair; lanes of
+// cells past the end compute on the last cell's data and store nothing.
+//
 // FIXUP = false: the pass, with FP32 weights; every tile writes its marks (write_marks) for the
 // cells at which a Gauss point left the FP32 range of the weights.  FIXUP = true: run right after
 // on the marked tiles (MarkScan), it redoes those cells with the weights in FP64 (a separate
-// instance keeps that code, and its call, out of the pass's register allocation); the decision
-// per cell keeps every cell's result independent of which cells share its tile.
+// instance keeps that code out of the pass's register allocation); the decision per cell keeps
+// every cell's result independent of which cells share its tile.
 template <int M, int G, bool WALLS, bool FIXUP>
 __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 / WENO_K1_TILE)
-    k_reconstruct_char_tma(const __grid_constant__ CUtensorMap map_gpm, const __grid_constant__ CUtensorMap map_dgs,
-                           const __grid_constant__ CUtensorMap map_g1, const __grid_constant__ CUtensorMap map_gop,
-                           const float* __restrict__ U, const float* __restrict__ Ulo,
-                           const int32_t* __restrict__ slot, const float* __restrict__ area, int64_t N,
-                           int64_t first, int64_t gbase, float* __restrict__ Wg, float eps, float gas_gamma,
-                           int linear, uint8_t* __restrict__ redo, uint8_t* __restrict__ cells,
-                           int* __restrict__ err, int stall) {
-  using L = CharTile<M, G>;
+    k_reconstruct_char_tma(const __grid_constant__ CUtensorMap map_gam, const __grid_constant__ CUtensorMap map_dg,
+                           const __grid_constant__ CUtensorMap map_gop, const float* __restrict__ U,
+                           const float* __restrict__ Ulo, const int32_t* __restrict__ slot,
+                           const float* __restrict__ area, int64_t N, int64_t first, int64_t gbase,
+                           float* __restrict__ Wg, float eps, float gas_gamma, int linear,
+                           uint8_t* __restrict__ redo, uint8_t* __restrict__ cells, int* __restrict__ err,
+                           int stall) {
+  using L = PairTile<M, G>;
   static_assert(L::TILE % 8 == 0, "a byte of cell marks per 8 cells");
-  constexpr int P = (M + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::STAGE);
   const int tid = threadIdx.x, base = (tid & 31) & ~3, l = tid & 3, cl = tid >> 2;
@@ -1160,19 +1261,17 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
   __syncthreads();
   auto issue = [&](int64_t tile) {
     mbar_expect_tx(&bar[0], L::STAGE);
-    tma_load_2d(smem, &map_gpm, (int)(tile * L::TILE * 4), 0, &bar[0]);
-    tma_load_2d(smem + L::GPM, &map_dgs, (int)(tile * L::TILE * 4), 0, &bar[0]);
-    if (M % 4) tma_load_2d(smem + L::GPM + L::DGS, &map_g1, (int)(tile * L::TILE * 2), 0, &bar[0]);
-    tma_load_2d(smem + L::GPM + L::DGS + L::G1, &map_gop, (int)(tile * L::TILE * 4), 0, &bar[0]);
+    tma_load_2d(smem, &map_gam, (int)(tile * L::TILE * 4), 0, &bar[0]);
+    tma_load_2d(smem + L::GAM, &map_dg, (int)(tile * L::TILE * 4), 0, &bar[0]);
+    tma_load_2d(smem + L::GAM + L::DG, &map_gop, (int)(tile * L::TILE * 4), 0, &bar[0]);
   };
   MarkScan scan(redo, ntiles);
   int64_t tile = FIXUP ? scan.next() : (int64_t)blockIdx.x;
   if (!FIXUP && tid == 0 && tile < ntiles) issue(tile);
   uint32_t phase = 0u;
-  const float4* sgp = reinterpret_cast<const float4*>(smem);
-  const float4* sds = reinterpret_cast<const float4*>(smem + L::GPM);
-  const float2* sg1 = reinterpret_cast<const float2*>(smem + L::GPM + L::DGS);
-  const float4* sgo = reinterpret_cast<const float4*>(smem + L::GPM + L::DGS + L::G1);
+  const float4* sgam = reinterpret_cast<const float4*>(smem);
+  const float4* sdg = reinterpret_cast<const float4*>(smem + L::GAM);
+  const float4* sgo = reinterpret_cast<const float4*>(smem + L::GAM + L::DG);
   for (; tile < ntiles; tile = FIXUP ? scan.next() : tile + gridDim.x) {
     if (FIXUP && tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the previous tile's reads
@@ -1200,75 +1299,39 @@ __global__ void __launch_bounds__(WENO_K1_TILE * 4, WENO_KCHAR_MIN_BLOCKS * 64 /
       if (tid == 0) *err = 1;
       return;
     }
-    // the Gauss points of face k in the frame of that face; FP64 = true evaluates the nonlinear
-    // weights in FP64 (the rare second pass), and returns the smallest sum of alpha otherwise
-    auto face = [&](int k, auto fp64_tag) -> float {
-      constexpr bool FP64 = decltype(fp64_tag)::value;
+    bool inrange = true;  // every sum of alpha of this lane's Gauss points within the FP32 range
+#pragma unroll 1
+    for (int k = 0; k < G / 2; ++k) {
+      // the frame of face k: the neighbour across it (slot k + 1) and the unit normal from the
+      // direction x_G' - x_G of its two Gauss points
       float Wn[4];
-      slot_state4<float, WALLS>(U, __ldg(slot + (int64_t)k * N + q), Wn);  // slot k+1: across face k
-      const float4 d0 = sds[(2 * k) * L::TILE + cl], d1 = sds[(2 * k + 1) * L::TILE + cl];
-      const float tx = d1.x - d0.x, ty = d1.y - d0.y, it = rsqrtf(tx * tx + ty * ty);
+      slot_state4<float, WALLS>(U, __ldg(slot + (int64_t)k * N + q), Wn);
+      const float4 d0 = sdg[(2 * k) * L::TILE + cl];
+      const float tx = d0.y - d0.x, ty = d0.w - d0.z, it = rsqrtf(tx * tx + ty * ty);
       float Lr[4], Rr[4];
       roe_rows<float>(W0, Wn, ty * it, -tx * it, gas_gamma - 1.f, l, Lr, Rr);
       float dU[M + 1];
       dU[0] = 0.f;
 #pragma unroll
       for (int s = 1; s <= M; ++s) dU[s] = lane_sum4(Lr, dW[s], base);
-      CandPairs<P> cp;
-      float gx[2 * P], gy[2 * P], b[2 * P];
-#pragma unroll
-      for (int j = 0; j < M; ++j) {
-        const float da = dU[Sub<M>::a(j)], db = dU[Sub<M>::b(j)];
-        const float4 m = sgo[j * L::TILE + cl];
-        gx[j] = fmaf(m.x, da, m.y * db);
-        gy[j] = fmaf(m.z, da, m.w * db);
-        b[j] = a0 * fmaf(gx[j], gx[j], gy[j] * gy[j]);
+      float2 incr;
+      if constexpr (FIXUP) {
+        if (act)
+          face_pair_fp64<M>(sgam, sdg, sgo, cl, k, dU, a0, eps, incr);
+        else
+          incr = f2(0.f, 0.f);
+      } else {
+        inrange = face_pair<M>(sgam, sdg, sgo, cl, k, dU, a0, eps, linear, incr) && inrange;
       }
-      if (M % 2) { gx[M] = 0.f; gy[M] = 0.f; b[M] = 0.f; }
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        cp.gx[p] = f2(gx[2 * p], gx[2 * p + 1]);
-        cp.gy[p] = f2(gy[2 * p], gy[2 * p + 1]);
-        cp.b[p] = f2(b[2 * p], b[2 * p + 1]);
-        cp.be[p] = __fadd2_rn(cp.b[p], f2(eps, eps));
+      const float d0l = lane_sum4(Rr, incr.x, base), d1l = lane_sum4(Rr, incr.y, base);  // variable l of R dU
+      if (act) {
+        Wg[(gbase + q * G + 2 * k) * 4 + l] = w0 + (l0 + d0l);
+        Wg[(gbase + q * G + 2 * k + 1) * 4 + l] = w0 + (l0 + d1l);
       }
-      float amin = 1.0f;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int g = 2 * k + h;
-        const float4 d = h ? d1 : d0;
-        float2 gp[P], gn[P];
-#pragma unroll
-        for (int kk = 0; kk < L::M4; ++kk) {
-          const float4 x = sgp[(g * 2 * L::M4 + kk) * L::TILE + cl];
-          const float4 y = sgp[(g * 2 * L::M4 + L::M4 + kk) * L::TILE + cl];
-          gp[2 * kk] = f2(x.x, x.y); gp[2 * kk + 1] = f2(x.z, x.w);
-          gn[2 * kk] = f2(y.x, y.y); gn[2 * kk + 1] = f2(y.z, y.w);
-        }
-        if (M % 4) {
-          const float2 e = sg1[g * L::TILE + cl];
-          gp[P - 1] = f2(e.x, 0.f);
-          gn[P - 1] = f2(e.y, 0.f);
-        }
-        float incr;
-        if constexpr (FP64) {
-          incr = act ? gauss_increment_fp64<P>(cp, gp, gn, d.x, d.y, d.z, d.w, eps) : 0.f;
-        } else {
-          float am;
-          incr = gauss_increment<M>(cp, gp, gn, d.x, d.y, d.z, d.w, linear, am);
-          amin = fminf(amin, am);
-        }
-        const float dWl = lane_sum4(Rr, incr, base);
-        if (act) Wg[(gbase + q * G + g) * 4 + l] = w0 + (l0 + dWl);
-      }
-      return amin;
-    };
-    float amin = 1.0f;
-#pragma unroll 1
-    for (int k = 0; k < G / 2; ++k) amin = fminf(amin, face(k, std::integral_constant<bool, FIXUP>{}));
+    }
     // weights outside the FP32 range at a cell of the tile (rare): the fix-up pass redoes the cell
     // (any of its four lanes).  Lanes past the end read the zero fill of the tables and are left out.
-    if constexpr (!FIXUP) write_marks<L::TILE>(act && !(amin >= kAlphaMin), tile, redo, cells);
+    if constexpr (!FIXUP) write_marks<L::TILE>(act && !inrange, tile, redo, cells);
     __syncthreads();  // the buffer is free for the next tile's copy
     if (!FIXUP && tid == 0 && next < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -99,9 +99,8 @@ struct weno_solver_s {
   void *q_pgam = nullptr, *q_pdg = nullptr, *t_pgam = nullptr, *t_pdg = nullptr;  // point-pair tables (Euler FP32C)
   int64_t q_pitch = 0, t_pitch = 0;  // row pitch (cells) of the packed FP32C tables
   bool tma = false;                   // Euler FP32C: reconstruction with TMA-staged tables
-  CUtensorMap q_map_gpm{}, q_map_dgs{}, t_map_gpm{}, t_map_dgs{}, t_map_g1{};
   CUtensorMap q_map_gop{}, t_map_gop{};  // gradient operators
-  CUtensorMap q_map_pgam{}, q_map_pdg{}, t_map_pgam{}, t_map_pdg{};  // point-pair tables
+  CUtensorMap q_map_pgam{}, q_map_pdg{}, t_map_pgam{}, t_map_pdg{};  // point-pair tables (both FP32C Euler kernels)
   int* err = nullptr;                 // set by a kernel whose bounded wait timed out
   uint8_t* char_redo = nullptr;       // FP32C characteristic tiles whose weights left the FP32 range
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
@@ -168,12 +167,12 @@ static_assert(weno::dev::kDevFlipX == weno::kFlipX && weno::dev::kDevFlipY == we
 // triangles): one byte per tile, then one bit per cell of the tile, each part padded to 16
 // bytes; zero bytes for every other path.
 int64_t redo_part(int64_t n) {
-  constexpr int64_t t = weno::dev::CharTile<12, 8>::TILE;
+  constexpr int64_t t = weno::dev::PairTile<12, 8>::TILE;
   const int64_t tiles = (n + t - 1) / t;
   return (tiles + 15) / 16 * 16 + (tiles * (t / 8) + 15) / 16 * 16;
 }
 int64_t redo_tiles_part(int64_t n) {
-  constexpr int64_t t = weno::dev::CharTile<12, 8>::TILE;
+  constexpr int64_t t = weno::dev::PairTile<12, 8>::TILE;
   return ((n + t - 1) / t + 15) / 16 * 16;
 }
 int64_t redo_bytes(const S& s) {
@@ -182,7 +181,7 @@ int64_t redo_bytes(const S& s) {
 }
 // Grid of a fix-up pass over n cells: a block per kFixupChunk tiles of marks, at most 4 per SM.
 unsigned fix_grid(const S& s, int64_t n) {
-  constexpr int64_t t = weno::dev::CharTile<12, 8>::TILE;
+  constexpr int64_t t = weno::dev::PairTile<12, 8>::TILE;
   const int64_t chunks = ((n + t - 1) / t + weno::dev::kFixupChunk - 1) / weno::dev::kFixupChunk;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, 4 * s.nsm));
 }
@@ -199,26 +198,26 @@ void launch_reconstruct_impl(S& s, const void* U, const void* Ulo, void* wg, cud
     if (s.prm.characteristic) {
       const T gg = (T)s.prm.gas_gamma;
       if constexpr (COMP) {  // packed FP32C tables staged by TMA (setup_tma runs for every FP32C Euler solver)
-        using CQ = weno::dev::CharTile<12, 8>;
-        using CT = weno::dev::CharTile<9, 6>;
+        using CQ = weno::dev::PairTile<12, 8>;
+        using CT = weno::dev::PairTile<9, 6>;
         // each pass is followed by its fix-up pass over the tiles it marked (a few us when none is)
         uint8_t* cells_q = redo + redo_tiles_part(s.nQ);
         uint8_t* redo_t = redo + redo_part(s.nQ);
         uint8_t* cells_t = redo_t + redo_tiles_part(s.nT);
         if (s.nQ && (which & 1)) {
           weno::dev::k_reconstruct_char_tma<12, 8, WALLS, false><<<tma_grid(s.k1q, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
-              s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
+              s.q_map_pgam, s.q_map_pdg, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
               (float*)wg, eps, gg, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
           weno::dev::k_reconstruct_char_tma<12, 8, WALLS, true><<<fix_grid(s, s.nQ), CQ::THREADS, CQ::SMEM, st>>>(
-              s.q_map_gpm, s.q_map_dgs, s.q_map_dgs, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
+              s.q_map_pgam, s.q_map_pdg, s.q_map_gop, u, ul, s.q_slot, (const float*)s.area, s.nQ, 0, 0,
               (float*)wg, eps, gg, s.prm.linear, redo, cells_q, s.err, s.debug_stall);
         }
         if (s.nT && (which & 2)) {
           weno::dev::k_reconstruct_char_tma<9, 6, WALLS, false><<<tma_grid(s.k1t, s.nT), CT::THREADS, CT::SMEM, st>>>(
-              s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
+              s.t_map_pgam, s.t_map_pdg, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
               8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
           weno::dev::k_reconstruct_char_tma<9, 6, WALLS, true><<<fix_grid(s, s.nT), CT::THREADS, CT::SMEM, st>>>(
-              s.t_map_gpm, s.t_map_dgs, s.t_map_g1, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
+              s.t_map_pgam, s.t_map_pdg, s.t_map_gop, u, ul, s.t_slot, (const float*)s.area, s.nT, s.nQ,
               8 * s.nQ, (float*)wg, eps, gg, s.prm.linear, redo_t, cells_t, s.err, s.debug_stall);
         }
       } else {
@@ -583,17 +582,6 @@ int setup_tma(S& s) {
   for (auto fn : {weno::dev::k_reconstruct_tma<9, 6, false, false>, weno::dev::k_reconstruct_tma<9, 6, true, false>,
                   weno::dev::k_reconstruct_tma<9, 6, false, true>, weno::dev::k_reconstruct_tma<9, 6, true, true>})
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM));
-  // the characteristic kernel's rows: gamma+-: G * 2 * (M/4) float4 rows; (x_G - c0, sigma+-): G
-  // float4 rows; triangle extras: G float2 rows
-  if (s.prm.characteristic && s.nQ) {
-    if ((r = make_map_2d(enc, &s.q_map_gpm, s.q_gam, 4 * s.q_pitch, 8 * 6, 16 * s.q_pitch, 4 * kTile, 8 * 6))) return r;
-    if ((r = make_map_2d(enc, &s.q_map_dgs, s.q_dg, 4 * s.q_pitch, 8, 16 * s.q_pitch, 4 * kTile, 8))) return r;
-  }
-  if (s.prm.characteristic && s.nT) {
-    if ((r = make_map_2d(enc, &s.t_map_gpm, s.t_gam, 4 * s.t_pitch, 6 * 4, 16 * s.t_pitch, 4 * kTile, 6 * 4))) return r;
-    if ((r = make_map_2d(enc, &s.t_map_dgs, s.t_dg, 4 * s.t_pitch, 6, 16 * s.t_pitch, 4 * kTile, 6))) return r;
-    if ((r = make_map_2d(enc, &s.t_map_g1, s.t_gam1, 2 * s.t_pitch, 6, 8 * s.t_pitch, 2 * kTile, 6))) return r;
-  }
   // D_j^+ rows: M float4 rows
   if (s.nQ && (r = make_map_2d(enc, &s.q_map_gop, s.q_gop, 4 * s.q_pitch, 12, 16 * s.q_pitch, 4 * kTile, 12)))
     return r;
@@ -604,12 +592,12 @@ int setup_tma(S& s) {
                     weno::dev::k_reconstruct_char_tma<12, 8, true, false>,
                     weno::dev::k_reconstruct_char_tma<12, 8, false, true>,
                     weno::dev::k_reconstruct_char_tma<12, 8, true, true>})
-      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::CharTile<12, 8>::SMEM));
+      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::PairTile<12, 8>::SMEM));
     for (auto fn : {weno::dev::k_reconstruct_char_tma<9, 6, false, false>,
                     weno::dev::k_reconstruct_char_tma<9, 6, true, false>,
                     weno::dev::k_reconstruct_char_tma<9, 6, false, true>,
                     weno::dev::k_reconstruct_char_tma<9, 6, true, true>})
-      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::CharTile<9, 6>::SMEM));
+      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, weno::dev::PairTile<9, 6>::SMEM));
   }
   s.tma = true;
   return WENO_OK;
@@ -853,9 +841,9 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   } else {
     d.q_pitch = (d.nQ + 63) / 64 * 64;
     d.t_pitch = (d.nT + 63) / 64 * 64;
-    // the split-weight rows of upload_packed serve the scalar and the characteristic kernels; the
-    // component-wise Euler kernel reads the point-pair tables
-    const bool rows = d.nv != 4 || p.characteristic;
+    // the split-weight rows of upload_packed serve the scalar kernel; both Euler kernels
+    // (component-wise and characteristic) read the point-pair tables
+    const bool rows = d.nv != 4;
     if ((r = upload_packed(d, tq, d.q_pitch, p.theta, &d.q_gop, &d.q_dg, &d.q_gam, &d.q_gam1, st, rows))) return r;
     if ((r = upload_packed(d, tt, d.t_pitch, p.theta, &d.t_gop, &d.t_dg, &d.t_gam, &d.t_gam1, st, rows))) return r;
     if (d.nv == 4) {
