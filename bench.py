@@ -691,10 +691,11 @@ def run_dmr(args):
     x_top = 1.0 / 6.0 + (1.0 + 20.0 * T) / np.sqrt(3.0)
     out = []
     for k in [int(x) for x in args.dmr_h.split(",")]:
-        for kind in ("quad", "tri"):
+        for kind in args.dmr_kinds.split(","):
             h = 1.0 / k
             diag = None if args.dmr_diagonal == "random" else int(args.dmr_diagonal)
-            mi = S.tube_mesh(4 * k, k, (4.0, 1.0), kind, args.dmr_delta, seed=4, walls=(2,),
+            ny = int(round(2.0 * k / np.sqrt(3.0))) if kind == "rowtri" else k  # rows of equilateral height
+            mi = S.tube_mesh(4 * k, ny, (4.0, 1.0), kind, args.dmr_delta, seed=4, walls=(2,),
                              wall_from=(0, 0, 1.0 / 6.0, 0), inflow=(0, 2, 3), diagonal=diag)
             mesh = Mesh.from_input(mi)
             W0 = S.cell_average(mi, d["f"], order=4)
@@ -853,6 +854,9 @@ def parse_args(argv=None):
     ap.add_argument("--dmr", action="store_true", help="double Mach reflection (inflow sides, partial wall)")
     ap.add_argument("--dmr-h", default="100,200", help="1/h of the double Mach reflection meshes")
     ap.add_argument("--dmr-fp64-max", type=int, default=100, help="largest 1/h run in FP64 as well")
+    ap.add_argument("--dmr-kinds", default="quad,tri",
+                    help="meshes of the double Mach reflection: quad, tri (split quads), rowtri (rows of "
+                         "near-equilateral triangles)")
     ap.add_argument("--dmr-image-dir", default="", help="write density images (PNG) of the FP32C runs here")
     ap.add_argument("--dmr-delta", type=float, default=0.1, help="node perturbation of the DMR meshes (0: regular)")
     ap.add_argument("--dmr-diagonal", default="random", choices=["random", "0", "1"],

@@ -17,7 +17,7 @@ import math
 import numpy as np
 
 __all__ = ["MeshInput", "quad_grid", "perturbed_quads", "split_quads", "stretched_vortex_mesh",
-           "mesh_for_config", "batch_instances", "tube_mesh"]
+           "mesh_for_config", "batch_instances", "tube_mesh", "row_triangles"]
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -216,12 +216,57 @@ def _vortex_maps(L: float, a: float = 9.0 / 11.0):
     return g, gy
 
 
+def row_triangles(nx: int, ny: int, extent):
+    """Box [0, Lx] x [0, Ly] of near-equilateral triangles: ny rows of height Ly / ny; the nodes of
+    even rows at x = i Lx / nx, those of odd rows shifted by half a spacing, plus a node on each
+    side (so every row ends on the box sides with a half-width triangle).  Counter-clockwise.
+    Returns (nodes, cell_nodes (n, 3))."""
+    Lx, Ly = (float(v) for v in extent)
+    hx = Lx / nx
+    xs_even = np.arange(nx + 1) * hx
+    xs_odd = np.concatenate([[0.0], (np.arange(nx) + 0.5) * hx, [Lx]])
+    nodes, rows, first = [], [], 0
+    for j in range(ny + 1):
+        xs = xs_even if j % 2 == 0 else xs_odd
+        rows.append((xs, first + np.arange(xs.size)))
+        nodes.append(np.stack([xs, np.full(xs.size, j * Ly / ny)], axis=1))
+        first += xs.size
+    cells = []
+    for j in range(ny):
+        (xa, ia), (xb, ib) = rows[j], rows[j + 1]
+        a = b = 0
+        while a < xa.size - 1 or b < xb.size - 1:  # sweep both rows in x: each step adds one triangle
+            na = xa[a + 1] if a < xa.size - 1 else np.inf
+            nb = xb[b + 1] if b < xb.size - 1 else np.inf
+            if na <= nb:
+                cells.append((ia[a], ia[a + 1], ib[b]))
+                a += 1
+            else:
+                cells.append((ia[a], ib[b + 1], ib[b]))
+                b += 1
+    pos = np.concatenate(nodes)
+    cn = np.array(cells, dtype=np.int64)
+    p = pos[cn]
+    cross = (p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) - (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1])
+    cn[cross < 0] = cn[cross < 0][:, [0, 2, 1]]
+    return pos, cn
+
+
 def tube_mesh(nx: int, ny: int, extent, kind="quad", delta=0.1, seed=0, walls=(), wall_from=(0.0, 0.0, 0.0, 0.0),
               inflow=(), diagonal=None):
     """Outflow box [0, Lx] x [0, Ly] of nx x ny perturbed quads (kind "quad"), all split into
     triangles ("tri") or 30 % split ("mixed"), along random diagonals or the one `diagonal` names
-    (see split_quads); `walls`, `wall_from` and `inflow` name reflective and inflow sides (see
-    MeshInput)."""
+    (see split_quads), or of near-equilateral triangles in ny rows ("rowtri", see row_triangles;
+    delta and diagonal do not apply); `walls`, `wall_from` and `inflow` name reflective and inflow
+    sides (see MeshInput)."""
+    if kind == "rowtri":
+        pos, cn = row_triangles(nx, ny, extent)
+        mi = MeshInput(pos, np.arange(0, 3 * cn.shape[0] + 1, 3, dtype=np.int64), cn.reshape(-1), "outflow",
+                       (0.0, 0.0), tuple(extent), f"tube-rowtri-{nx}x{ny}", seed, {"nx": nx, "ny": ny})
+        mi.walls = tuple(walls)
+        mi.wall_from = tuple(float(v) for v in wall_from)
+        mi.inflow = tuple(inflow)
+        return mi
     frac = {"quad": 0.0, "tri": 1.0, "mixed": 0.3}[kind]
     pos, quads = perturbed_quads(nx, (0.0, 0.0), tuple(extent), delta, seed, ny=ny)
     mi = _assemble(pos, quads, frac, seed, "outflow", (0.0, 0.0), tuple(extent), f"tube-{kind}-{nx}x{ny}",

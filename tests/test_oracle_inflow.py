@@ -118,12 +118,13 @@ def test_planar_shock_carried_by_the_moving_boundary_state():
 
 def test_double_mach_initial_shock_positivity_finding():
     """Recorded behaviour of the scheme (no limiter) on the double Mach data at t = 0: Gauss values
-    with p <= 0 appear on cells straddling the Mach 10 shock for triangles with either variable set and
-    for quads component-wise, but not for quads with characteristic variables, the only combination
-    that runs to t = 0.2 through the CUDA path."""
+    with p <= 0 appear on cells straddling the Mach 10 shock for split-quad triangles with either
+    variable set and for quads component-wise, but not for quads with characteristic variables, the
+    only combination that runs to t = 0.2 through the CUDA path, nor for rows of near-equilateral
+    triangles with characteristic variables (which start, but lose positivity after about 85 steps)."""
     d = S.double_mach()
     bad = {}
-    for kind in ("tri", "quad"):
+    for kind in ("tri", "quad", "rowtri"):
         mi = S.tube_mesh(40, 20, (1.0, 0.5), kind, 0.1, seed=4, walls=(2,), wall_from=(0, 0, 1.0 / 6.0, 0),
                          inflow=(0, 2, 3))
         m = OracleMesh.from_input(mi)
@@ -136,4 +137,4 @@ def test_double_mach_initial_shock_positivity_finding():
             lo = np.where(np.isfinite(p), np.minimum(p, Wg[0]), np.inf).min(axis=1)
             bad[kind, ch] = int((lo <= 0).sum())
     assert bad["tri", False] > 0 and bad["tri", True] > 0 and bad["quad", False] > 0, bad
-    assert bad["quad", True] == 0, bad
+    assert bad["quad", True] == 0 and bad["rowtri", True] == 0, bad
