@@ -204,9 +204,9 @@ int weno_residual(weno_solver_t s, const void* U, const void* U_lo, void* R, voi
  * they are running (a device-memory budget fixed at start-up, or a loop that
  * may not make allocation calls), and it allocates nothing itself.
  *  - Limit: (8 n_quads + 6 n_tris) * n_v + 256-byte padding + n_faces * n_v
- *    elements of 8 (FP64) or 4 (FP32C) bytes, plus for FP32C characteristic
- *    solvers about 3 bytes per 16 cells of marks (cells whose weights left
- *    the FP32 range), must fit in 16 MiB, i.e. about 50k cells for FP64 Euler
+ *    elements of 8 (FP64) or 4 (FP32C) bytes, plus for FP32C Euler solvers
+ *    about 3 bytes per 16 cells of marks (cells whose weights left the FP32
+ *    range), must fit in 16 MiB, i.e. about 50k cells for FP64 Euler
  *    and 100k for FP32C; larger meshes get WENO_EINVAL with the sizes in
  *    weno_last_error().
  *  - The first call on each device looks up the array's device address on

@@ -102,7 +102,7 @@ struct weno_solver_s {
   CUtensorMap q_map_gop{}, t_map_gop{};  // gradient operators
   CUtensorMap q_map_pgam{}, q_map_pdg{}, t_map_pgam{}, t_map_pdg{};  // point-pair tables (both FP32C Euler kernels)
   int* err = nullptr;                 // set by a kernel whose bounded wait timed out
-  uint8_t* char_redo = nullptr;       // FP32C characteristic tiles whose weights left the FP32 range
+  uint8_t* fix_marks = nullptr;       // FP32C Euler: tiles and cells whose weights left the FP32 range
   int32_t *q_slot = nullptr, *t_slot = nullptr, *q_cf = nullptr, *t_cf = nullptr;
   void *area = nullptr, *inv_area = nullptr, *inv_area_lo = nullptr;
   double* area64 = nullptr;
@@ -163,9 +163,9 @@ static_assert(weno::dev::kDevFlipX == weno::kFlipX && weno::dev::kDevFlipY == we
               "stencil table bit layout shared by the host tables and the kernels");
 
 // ------------------------------------------------------------ launches
-// Fix-up marks of the FP32C characteristic reconstruction, per cell group (quads, then
-// triangles): one byte per tile, then one bit per cell of the tile, each part padded to 16
-// bytes; zero bytes for every other path.
+// Fix-up marks of the FP32C Euler reconstructions (component-wise and characteristic), per cell
+// group (quads, then triangles): one byte per tile, then one bit per cell of the tile, each part
+// padded to 16 bytes; zero bytes for every other path.
 int64_t redo_part(int64_t n) {
   constexpr int64_t t = weno::dev::PairTile<12, 8>::TILE;
   const int64_t tiles = (n + t - 1) / t;
@@ -294,7 +294,7 @@ void launch_reconstruct_into(S& s, const void* U, const void* Ulo, void* wg, cud
 
 template <typename T, int NV, bool COMP>
 void launch_reconstruct(S& s, const void* U, const void* Ulo, cudaStream_t st, int which = 3) {
-  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, s.Wg, st, which, s.char_redo);
+  launch_reconstruct_into<T, NV, COMP>(s, U, Ulo, s.Wg, st, which, s.fix_marks);
 }
 
 // Face fluxes of the Gauss values wg into fl; c places the stage in the step (time t + c dt).
@@ -967,7 +967,7 @@ int weno_solver_create(weno_mesh_t mesh, const weno_params* params, void* cuda_s
   CK(cudaMemsetAsync(d.flag, 0, sizeof(int) * d.n_inst, st));
   if ((r = d.alloc(&d.err, sizeof(int)))) return r;
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), st));
-  if (redo_bytes(d) && (r = d.alloc(&d.char_redo, (size_t)redo_bytes(d)))) return r;
+  if (redo_bytes(d) && (r = d.alloc(&d.fix_marks, (size_t)redo_bytes(d)))) return r;
   if (!d.fp64 && d.nv == 4 && (r = setup_tma(d))) return r;
   CK(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
   CK(cudaStreamSynchronize(st));
@@ -1273,8 +1273,8 @@ void launch_residual_static(S& s, const void* U, const void* Ulo, void* R, void*
 
 extern "C" int weno_residual_static(weno_solver_t s, const void* U, const void* U_lo, void* R, void* cuda_stream) {
   if (!s || !U || !R || (!s->fp64 && !U_lo)) return fail(WENO_EINVAL, "null argument");
-  // Gauss-point values first, face fluxes after them on a 256-byte boundary, then (FP32C
-  // characteristic solvers) the reconstruction's fix-up marks, a byte per tile and a bit per cell
+  // Gauss-point values first, face fluxes after them on a 256-byte boundary, then (FP32C Euler
+  // solvers) the reconstruction's fix-up marks, a byte per tile and a bit per cell
   const size_t wg_bytes = (size_t)(8 * s->nQ + 6 * s->nT) * s->nv * s->esz;
   const size_t f_off = (wg_bytes + 255) / 256 * 256;
   const size_t r_off = (f_off + (size_t)s->nF * s->nv * s->esz + 255) / 256 * 256;
