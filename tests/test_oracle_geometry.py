@@ -86,3 +86,19 @@ def test_cell_gauss_points_match_across_faces():
         xl = m.cell_gauss[L, [2 * kL, 2 * kL + 1]]
         xr = m.cell_gauss[R, [2 * kR + 1, 2 * kR]] + m.face_shift[f]
         assert np.allclose(xl, xr, atol=1e-13)
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 5), (7, 6)])
+def test_row_triangle_box(nx, ny):
+    """Rows of near-equilateral triangles on a box: counter-clockwise, tiling the box exactly
+    (areas sum to it), Euler's formula for a disc, 2 nx + 1 triangles per row, and boundary faces
+    exactly on the box sides: nx on the bottom, nx or nx + 1 on the top (an odd top row holds
+    nx + 2 nodes), one per row on each vertical side."""
+    mi = S.tube_mesh(nx, ny, (2.0, 1.0), "rowtri")
+    m = OracleMesh.from_input(mi)
+    assert (m.cell_size == 3).all() and m.area.min() > 0
+    assert m.area.sum() == pytest.approx(2.0, rel=1e-13)
+    assert mi.n_nodes - m.n_faces + m.n_cells == 1
+    assert m.n_cells == ny * (2 * nx + 1)
+    top = nx if ny % 2 == 0 else nx + 1
+    assert int((m.face_R < 0).sum()) == nx + top + 2 * ny
