@@ -191,3 +191,21 @@ def test_fp32c_solver_needs_eps_of_at_least_1e_15(lib):
     p = params_struct(precision="fp32c", eps=1e-20)
     assert lib.weno_solver_create(m._h, ctypes.byref(p), None, ctypes.byref(h)) == _capi.WENO_EINVAL
     assert b"1e-15" in lib.weno_last_error()
+
+
+def test_host_precompute_matches_oracle_on_row_triangles_with_walls():
+    """The same comparison on rows of near-equilateral triangles (every node of valence 6 inside,
+    half-width triangles on the sides) in a box with a partial wall and inflow sides, the double
+    Mach reflection's boundary layout."""
+    from paper_1712_08317_gb300.api import Mesh
+    mi = S.tube_mesh(12, 8, (2.0, 1.0), "rowtri", walls=(2,), wall_from=(0, 0, 1.0 / 3.0, 0), inflow=(0, 2, 3))
+    m = Mesh.from_input(mi)
+    raw, opt = m.weight_stats()
+    groups = precompute(OracleMesh.from_input(mi), Params())
+    oraw = np.zeros(mi.n_cells)
+    oopt = np.zeros(mi.n_cells)
+    for t in groups:
+        oraw[t.cells] = np.abs(t.gamma_raw).max(axis=(1, 2))
+        oopt[t.cells] = np.abs(t.gamma).max(axis=(1, 2))
+    assert np.allclose(raw, oraw[m.perm], rtol=1e-10, atol=1e-12)
+    assert np.allclose(opt, oopt[m.perm], rtol=1e-10, atol=1e-12)
