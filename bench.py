@@ -744,6 +744,31 @@ def run_dmr(args):
     print(json.dumps({"dmr": out, "t": T, "cfl": args.cfl}), flush=True)
 
 
+def run_free_stream(args):
+    """Residual of a uniform flow (rho = u = v = p = 1) through the CUDA path, FP64 and FP32C, on
+    periodic [0,10]^2 meshes with n = 320 (regular and irregular quads and split triangles): exact
+    arithmetic gives 0, so the result is the rounding level of each precision's residual."""
+    import synthetic as S
+    from paper_1712_08317_gb300.api import Mesh, Solver
+    out = {}
+    for name, kind, delta, diag in (("quad-reg", "quad", 0.0, None), ("quad-irr", "quad", 0.1, None),
+                                    ("tri-reg", "tri", 0.0, 0), ("tri-irr", "tri", 0.1, None)):
+        mi = S.periodic_mesh(args.fs_n, 10.0, kind, delta, seed=0, diagonal=diag)
+        mesh = Mesh.from_input(mi)
+        W = np.zeros((4, mi.n_cells))
+        W[0] = W[1] = W[2] = 1.0
+        W[3] = 1.0 / 0.4 + 1.0
+        row = {"cells": mi.n_cells, "h": 10.0 / args.fs_n}
+        for prec in ("fp64", "fp32c"):
+            sol = Solver(mesh, eqn="euler", precision=prec)
+            U, Ul = sol.to_device(W)
+            R = sol.to_host(sol.residual(U, Ul))
+            row[prec] = {"max_abs_R": float(np.abs(R).max()), "mean_abs_R": float(np.abs(R).mean())}
+        out[name] = row
+        print(json.dumps({"free_stream": {name: row}}), flush=True)
+    print(json.dumps({"free_stream": out, "state": "rho = u = v = p = 1"}), flush=True)
+
+
 def ladder_orders(rows, precisions):
     """Observed orders between consecutive rows of a ladder (mesh ratio from the cell counts)."""
     for prec in precisions:
@@ -863,6 +888,8 @@ def parse_args(argv=None):
                     help="diagonal along which the DMR triangle meshes split their quads")
     ap.add_argument("--families", default="densitywave-tri,vortex-lowq")
     ap.add_argument("--vortex4m-t2", action="store_true", help="the benchmark workload in FP32C to t = 2 vs exact")
+    ap.add_argument("--free-stream", action="store_true", help="residual of a uniform flow, FP64 and FP32C")
+    ap.add_argument("--fs-n", type=int, default=320, help="mesh size n of the free-stream meshes")
     return ap.parse_args(argv)
 
 
@@ -885,6 +912,9 @@ def main():
         return
     if args.vortex4m_t2:
         run_vortex4m_t2(args)
+        return
+    if args.free_stream:
+        run_free_stream(args)
         return
     assert args.warmup >= 3, "at least 3 warm-up steps"
     import torch
